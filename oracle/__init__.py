@@ -1,0 +1,238 @@
+"""FP64 CPU oracle for the ELIBB lattice Boltzmann hot path (TEST INFRASTRUCTURE).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package. It shares no code with the CUDA library
+(``paper_2009_04604_gb300``) and neither imports the other.
+
+The arithmetic lives in ``lbm_oracle.c`` (plain C, ``-ffp-contract=off``); this
+module compiles it with gcc and wraps it with ctypes. Array conventions follow
+``lbm_oracle.h``: node ``n = x + nx*(y + ny*z)``, populations ``f[n, i]``,
+per-link data ``q[n, i]`` for the link from node ``n`` towards ``n - c_i``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liblbm_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+D2Q9, D3Q19 = 0, 1
+FLUID, SOLID, OPEN = 0, 1, 2
+BC_ELIBB_F, BC_ELIBB_FQ, BC_BFL, BC_HWBB, BC_ELIBB_U, BC_ELIBB_UQ = 0, 1, 2, 3, 4, 5
+SHAPE_SPHERE, SHAPE_SPHERE_OUT, SHAPE_ELLIPSOID, SHAPE_STRIP = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liblbm_oracle.so`` (gcc, OpenMP)."""
+    src = os.path.join(_HERE, "lbm_oracle.c")
+    hdr = os.path.join(_HERE, "lbm_oracle.h")
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(src), os.path.getmtime(hdr))):
+        return _LIB_PATH
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-fPIC", "-shared", src, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nz", ctypes.c_int), ("xshift", ctypes.c_int), ("bc", ctypes.c_int),
+                ("tau", ctypes.c_double), ("rho0", ctypes.c_double),
+                ("force", ctypes.c_double * 3), ("qcut", ctypes.c_double),
+                ("wall_neq_same", ctypes.c_int), ("me_rho0", ctypes.c_int),
+                ("s1_exact", ctypes.c_int)]
+
+
+class Shape(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("tag", ctypes.c_int),
+                ("c", ctypes.c_double * 3), ("r", ctypes.c_double * 3),
+                ("nrm", ctypes.c_double * 3), ("off", ctypes.c_double),
+                ("width", ctypes.c_double), ("period", ctypes.c_double),
+                ("v", ctypes.c_double * 3), ("om", ctypes.c_double * 3),
+                ("v1", ctypes.c_double * 3), ("om1", ctypes.c_double * 3)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.POINTER
+            d, i32, u8 = P(ctypes.c_double), P(ctypes.c_int32), P(ctypes.c_uint8)
+            lib.or_lattice.argtypes = [ctypes.c_int, P(ctypes.c_int), d, P(ctypes.c_int)]
+            lib.or_init_eq.argtypes = [P(Params), u8, d, d, d]
+            lib.or_step.argtypes = [P(Params), u8, d, d, d, d, d, d]
+            lib.or_macros.argtypes = [P(Params), u8, d, d, d]
+            lib.or_mass.argtypes = [P(Params), u8, d]
+            lib.or_mass.restype = ctypes.c_double
+            lib.or_refill.argtypes = [P(Params), u8, u8, d, d]
+            lib.or_geometry.argtypes = [P(Params), u8, d, P(Shape), ctypes.c_int, u8, d, d, d, i32]
+            lib.or_geometry.restype = ctypes.c_long
+            lib.or_bc_weights.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, d, d]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a, ctype):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _dp(a):
+    return _ptr(a, ctypes.c_double)
+
+
+def lattice(lat: int):
+    """Oracle lattice tables ``(c[Q,3] int, w[Q], opp[Q])``."""
+    lib = _load()
+    c = np.zeros((19, 3), np.int32)
+    w = np.zeros(19)
+    opp = np.zeros(19, np.int32)
+    Qn = lib.or_lattice(lat, _ptr(c, ctypes.c_int), _dp(w), _ptr(opp, ctypes.c_int))
+    return c[:Qn].copy(), w[:Qn].copy(), opp[:Qn].copy()
+
+
+def params(lattice_id, dims, tau, bc=BC_ELIBB_F, rho0=1.0, force=(0.0, 0.0, 0.0), xshift=0,
+           qcut=0.01, wall_neq_same=0, me_rho0=0, s1_exact=0) -> Params:
+    nx, ny, nz = (list(dims) + [1, 1])[:3]
+    p = Params()
+    p.lattice, p.nx, p.ny, p.nz, p.xshift, p.bc = lattice_id, nx, ny, nz, xshift, bc
+    p.tau, p.rho0, p.qcut = tau, rho0, qcut
+    for a in range(3):
+        p.force[a] = float(force[a])
+    p.wall_neq_same, p.me_rho0, p.s1_exact = wall_neq_same, me_rho0, s1_exact
+    return p
+
+
+def _Q(p):
+    return 9 if p.lattice == D2Q9 else 19
+
+
+def _N(p):
+    return p.nx * p.ny * p.nz
+
+
+def _c8(a):
+    return np.ascontiguousarray(a, dtype=np.uint8)
+
+
+def _cd(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def init_eq(p, flags, rho=None, u=None):
+    f = np.zeros((_N(p), _Q(p)))
+    rho = _cd(None if rho is None else np.reshape(rho, -1))
+    u = _cd(None if u is None else np.reshape(u, (-1, 3)))
+    _load().or_init_eq(ctypes.byref(p), _ptr(_c8(flags), ctypes.c_uint8), _dp(rho), _dp(u), _dp(f))
+    return f
+
+
+def step(p, flags, f, q=None, uw=None, uw1=None, want_force=False):
+    """One update; returns ``fout`` or ``(fout, flink[N,Q,3])``."""
+    f = _cd(f)
+    fout = np.empty_like(f)
+    flink = np.zeros((_N(p), _Q(p), 3)) if want_force else None
+    rc = _load().or_step(ctypes.byref(p), _ptr(_c8(flags), ctypes.c_uint8), _dp(_cd(q)),
+                         _dp(_cd(uw)), _dp(_cd(uw1)), _dp(f), _dp(fout), _dp(flink))
+    if rc != 0:
+        raise ValueError("or_step rejected its arguments")
+    return (fout, flink) if want_force else fout
+
+
+def macros(p, flags, f):
+    rho = np.zeros(_N(p))
+    u = np.zeros((_N(p), 3))
+    _load().or_macros(ctypes.byref(p), _ptr(_c8(flags), ctypes.c_uint8), _dp(_cd(f)), _dp(rho), _dp(u))
+    return rho, u
+
+
+def mass(p, flags, f) -> float:
+    return _load().or_mass(ctypes.byref(p), _ptr(_c8(flags), ctypes.c_uint8), _dp(_cd(f)))
+
+
+def refill(p, flags_old, flags_new, un, f):
+    """In place: nodes that turned fluid get f^eq(rho0, un[n])."""
+    assert f.dtype == np.float64 and f.flags.c_contiguous
+    _load().or_refill(ctypes.byref(p), _ptr(_c8(flags_old), ctypes.c_uint8),
+                      _ptr(_c8(flags_new), ctypes.c_uint8), _dp(_cd(un)), _dp(f))
+    return f
+
+
+def make_shapes(specs):
+    """Build a ctypes array of Shape from dicts (keys as in ``Shape``)."""
+    arr = (Shape * max(1, len(specs)))()
+    for k, s in enumerate(specs):
+        for key, val in s.items():
+            if isinstance(val, (list, tuple, np.ndarray)):
+                dst = getattr(arr[k], key)
+                for a, x in enumerate(val):
+                    dst[a] = float(x)
+            else:
+                setattr(arr[k], key, val)
+    return arr
+
+
+def geometry(p, base=None, base_u=None, shapes=()):
+    """Flags and per-link q, u_w(t), u_w(t+1), tag from analytic shapes."""
+    N, Qn = _N(p), _Q(p)
+    flags = np.zeros(N, np.uint8)
+    q = np.zeros((N, Qn))
+    uw = np.zeros((N, Qn, 3))
+    uw1 = np.zeros((N, Qn, 3))
+    tag = np.zeros((N, Qn), np.int32)
+    arr = make_shapes(list(shapes))
+    base = None if base is None else _c8(np.reshape(base, -1))
+    base_u = _cd(None if base_u is None else np.reshape(base_u, (-1, 3)))
+    _load().or_geometry(ctypes.byref(p), _ptr(base, ctypes.c_uint8), _dp(base_u), arr, len(shapes),
+                        _ptr(flags, ctypes.c_uint8), _dp(q), _dp(uw), _dp(uw1),
+                        _ptr(tag, ctypes.c_int32))
+    return flags, q, uw, uw1, tag
+
+
+def bc_weights(bc, q, qcut=0.01):
+    """``[(s_j, a_j)]`` the boundary rule interpolates through at this q."""
+    s = np.zeros(3)
+    a = np.zeros(3)
+    npnt = _load().or_bc_weights(bc, q, qcut, _dp(s), _dp(a))
+    return list(zip(s[:npnt].tolist(), a[:npnt].tolist()))
+
+
+class Sim:
+    """Small driver holding an oracle state (flags, links, populations)."""
+
+    def __init__(self, p, flags, q=None, uw=None, uw1=None, f=None):
+        self.p = p
+        self.flags = _c8(np.reshape(flags, -1))
+        self.q, self.uw, self.uw1 = q, uw, uw1
+        self.f = init_eq(p, self.flags) if f is None else _cd(f)
+        self.t = 0
+
+    def run(self, n, want_force=False):
+        flink = None
+        for _ in range(n):
+            if want_force:
+                self.f, flink = step(self.p, self.flags, self.f, self.q, self.uw, self.uw1, True)
+            else:
+                self.f = step(self.p, self.flags, self.f, self.q, self.uw, self.uw1)
+            self.t += 1
+        return flink
+
+    def macros(self):
+        return macros(self.p, self.flags, self.f)
+
+    def mass(self):
+        return mass(self.p, self.flags, self.f)

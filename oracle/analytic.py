@@ -1,0 +1,54 @@
+"""Closed-form flows and error metrics used to pin the oracle (TEST INFRASTRUCTURE).
+
+Each function cites the passage (or textbook result) it restates.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def couette_impulsive(y, t, h, U, nu, nterms=100):
+    """Impulsively started plane Couette flow (Sec. III.A, Eq. solution-couette).
+
+    Lower wall at rest at y = 0, upper wall moving with U at y = h from t = 0;
+    series truncated at ``nterms`` terms (the paper uses 100).
+    """
+    y = np.asarray(y, dtype=np.float64)
+    s = y / h
+    for n in range(1, nterms + 1):
+        s = s + (2.0 / np.pi) * ((-1.0) ** n / n) * np.exp(-n * n * np.pi ** 2 * nu * t / h ** 2) \
+            * np.sin(n * np.pi * y / h)
+    return U * s
+
+
+def cylindrical_couette(r, r1, r2, omega1):
+    """Steady circular Couette flow, outer cylinder at rest (Sec. III.B):
+    u_theta = (r1^2 - beta^2 r^2) omega1 / ((1 - beta^2) r), beta = r1/r2."""
+    r = np.asarray(r, dtype=np.float64)
+    beta = r1 / r2
+    return (r1 ** 2 - beta ** 2 * r ** 2) * omega1 / ((1.0 - beta ** 2) * r)
+
+
+def couette_torque(rho0, nu, omega1, r1, r2):
+    """Torque per unit length on the inner cylinder of steady circular Couette flow
+    (textbook: 4 pi mu omega1 r1^2 r2^2 / (r2^2 - r1^2))."""
+    return 4.0 * np.pi * rho0 * nu * omega1 * r1 ** 2 * r2 ** 2 / (r2 ** 2 - r1 ** 2)
+
+
+def poiseuille_transient(s, t, W, g, nu, nterms=2001):
+    """Body-force driven channel flow from rest between no-slip walls at s = 0, W
+    (textbook sine-series solution of u_t = nu u_ss + g):
+    u = g s (W - s)/(2 nu) - sum_{k odd} 4 g W^2/(nu pi^3 k^3) sin(k pi s/W) e^{-k^2 pi^2 nu t/W^2}."""
+    s = np.asarray(s, dtype=np.float64)
+    u = g * s * (W - s) / (2.0 * nu)
+    for k in range(1, nterms + 1, 2):
+        u = u - 4.0 * g * W ** 2 / (nu * np.pi ** 3 * k ** 3) * np.sin(k * np.pi * s / W) \
+            * np.exp(-k * k * np.pi ** 2 * nu * t / W ** 2)
+    return u
+
+
+def rrse(u, u_th):
+    """Relative root squared error (Sec. III.A, Eq. rRMSE)."""
+    u = np.asarray(u, dtype=np.float64)
+    u_th = np.asarray(u_th, dtype=np.float64)
+    return float(np.sqrt(np.sum((u - u_th) ** 2) / np.sum(u_th ** 2)))

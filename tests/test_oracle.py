@@ -1,0 +1,477 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: every check is a closed form, an
+exact invariant, a brute-force computation, or a value the paper prints.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import analytic as A
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_lattice(name):
+    rows = []
+    for line in open(os.path.join(GOLDEN, name)):
+        if line.startswith("#") or not line.strip():
+            continue
+        cx, cy, cz, w = line.split()
+        rows.append(((int(cx), int(cy), int(cz)), Fraction(w)))
+    return rows
+
+
+# ---------------------------------------------------------------- lattice tables
+@pytest.mark.parametrize("lat,name", [(oracle.D2Q9, "d2q9.txt"), (oracle.D3Q19, "d3q19.txt")])
+def test_lattice_matches_textbook(oracle_lib, lat, name):
+    c, w, opp = oracle.lattice(lat)
+    gold = {cv: wv for cv, wv in _read_lattice(name)}
+    assert len(gold) == len(w)
+    for i in range(len(w)):
+        assert float(gold[tuple(int(v) for v in c[i])]) == pytest.approx(w[i], abs=1e-16)
+        assert (c[opp[i]] == -c[i]).all()
+
+
+@pytest.mark.parametrize("lat", [oracle.D2Q9, oracle.D3Q19])
+def test_lattice_isotropy(oracle_lib, lat):
+    """Moments of the weights: sum w = 1, sum w c_a c_b = cs2 delta, 4th-order isotropy."""
+    c, w, _ = oracle.lattice(lat)
+    D = 2 if lat == oracle.D2Q9 else 3
+    c = c[:, :D].astype(float)
+    cs2 = 1.0 / 3.0
+    assert w.sum() == pytest.approx(1.0, abs=1e-15)
+    assert np.abs(np.einsum("i,ia->a", w, c)).max() < 1e-16
+    np.testing.assert_allclose(np.einsum("i,ia,ib->ab", w, c, c), cs2 * np.eye(D), atol=1e-16)
+    assert np.abs(np.einsum("i,ia,ib,ic->abc", w, c, c, c)).max() < 1e-16
+    d = np.eye(D)
+    iso = cs2 ** 2 * (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+                      + np.einsum("ad,bc->abcd", d, d))
+    np.testing.assert_allclose(np.einsum("i,ia,ib,ic,id->abcd", w, c, c, c, c), iso, atol=1e-16)
+
+
+@pytest.mark.parametrize("lat", [oracle.D2Q9, oracle.D3Q19])
+def test_equilibrium_moments(oracle_lib, lat):
+    """Eq. Eq2ndOrder: sum f^eq = rho, sum c f^eq = rho u, sum c c f^eq = rho (cs2 I + u u)."""
+    Qn = 9 if lat == oracle.D2Q9 else 19
+    D = 2 if lat == oracle.D2Q9 else 3
+    rng = np.random.default_rng(1)
+    n = 7
+    rho = 1.0 + 0.1 * rng.standard_normal(n)
+    u = 0.05 * rng.standard_normal((n, 3))
+    if D == 2:
+        u[:, 2] = 0.0
+    p = oracle.params(lat, (n, 1, 1), 0.8)
+    f = oracle.init_eq(p, np.zeros(n, np.uint8), rho, u)
+    c, w, _ = oracle.lattice(lat)
+    c = c.astype(float)
+    np.testing.assert_allclose(f.sum(1), rho, rtol=1e-15)
+    np.testing.assert_allclose(f @ c, rho[:, None] * u, atol=1e-16)
+    P = np.einsum("ni,ia,ib->nab", f, c[:, :D], c[:, :D])
+    ref = rho[:, None, None] * (np.eye(D) / 3.0 + np.einsum("na,nb->nab", u[:, :D], u[:, :D]))
+    np.testing.assert_allclose(P, ref, atol=1e-15)
+    assert f.shape == (n, Qn)
+
+
+# ---------------------------------------------------------------- interpolation weights
+def _printed():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "elibb_printed_weights.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        scheme, q, pt, a = line.split()
+        rows.append((scheme, Fraction(q), pt, Fraction(a)))
+    return rows
+
+
+_S_OF = {"F0": lambda q: 0.0, "G": lambda q: 1.0 - q, "F1": lambda q: 1.0, "H": lambda q: 1.0 + q,
+         "FF": lambda q: -q}
+_BC = {"U": oracle.BC_ELIBB_U, "F": oracle.BC_ELIBB_F, "BFL": oracle.BC_BFL}
+
+
+def test_weights_match_printed_formulas(oracle_lib):
+    """ELIBB-U (Sec. II.D), ELIBB-F (Eq. linear_broken_method, reading of the q>=1/2 typo)
+    and BFL (Eq. bfl) weights as printed by the paper."""
+    rows = _printed()
+    assert rows
+    for scheme, q, pt, a in rows:
+        got = dict((round(s, 12), w) for s, w in oracle.bc_weights(_BC[scheme], float(q)))
+        s = round(_S_OF[pt](float(q)), 12)
+        assert s in got, (scheme, q, pt)
+        assert got[s] == pytest.approx(float(a), abs=1e-14), (scheme, q, pt)
+
+
+@pytest.mark.parametrize("bc", [oracle.BC_ELIBB_F, oracle.BC_ELIBB_FQ, oracle.BC_BFL, oracle.BC_HWBB,
+                                oracle.BC_ELIBB_U, oracle.BC_ELIBB_UQ])
+def test_weights_partition_of_unity_and_polynomial_exactness(oracle_lib, bc):
+    """Lagrange weights (Eq. poli_coeff) reproduce every polynomial up to their degree."""
+    for q in [0.001, 0.01, 0.05, 0.2, 0.4999, 0.5, 0.5001, 0.8, 1.0]:
+        pts = oracle.bc_weights(bc, q)
+        s = np.array([p[0] for p in pts])
+        a = np.array([p[1] for p in pts])
+        assert a.sum() == pytest.approx(1.0, abs=1e-13)
+        for k in range(len(pts)):
+            assert (a * s ** k).sum() == pytest.approx(q ** k, abs=1e-12)
+
+
+@pytest.mark.parametrize("bc", [oracle.BC_ELIBB_F, oracle.BC_ELIBB_FQ, oracle.BC_BFL, oracle.BC_HWBB])
+def test_half_way_limit(oracle_lib, bc):
+    """At q = 1/2 every fragmented scheme reduces to half-way bounce-back (Sec. II.B)."""
+    pts = dict((round(s, 12), a) for s, a in oracle.bc_weights(bc, 0.5))
+    assert pts[0.5] == pytest.approx(1.0, abs=1e-15)
+    assert sum(abs(v) for k, v in pts.items() if k != 0.5) < 1e-15
+
+
+def test_fq_equals_uq_below_half_and_cutoff(oracle_lib):
+    """ELIBB-FQ and ELIBB-UQ share their points for q < 1/2 (Sec. III.A); FQ falls back
+    to ELIBB-F below q_cut = 0.01 (Sec. II.D)."""
+    for q in [0.011, 0.1, 0.3, 0.49]:
+        assert oracle.bc_weights(oracle.BC_ELIBB_FQ, q) == oracle.bc_weights(oracle.BC_ELIBB_UQ, q)
+    for q in [0.001, 0.009]:
+        assert oracle.bc_weights(oracle.BC_ELIBB_FQ, q) == oracle.bc_weights(oracle.BC_ELIBB_F, q)
+    assert len(oracle.bc_weights(oracle.BC_ELIBB_FQ, 0.011)) == 3
+
+
+# ---------------------------------------------------------------- bulk invariants
+def _random_state(p, rng, amp=0.05):
+    Qn = 9 if p.lattice == oracle.D2Q9 else 19
+    N = p.nx * p.ny * p.nz
+    _, w, _ = oracle.lattice(p.lattice)
+    return w[None, :] * (1.0 + amp * rng.standard_normal((N, Qn)))
+
+
+def _shifted_neighbour(p, x, y, z, c):
+    """Brute-force node reached from (x, y, z) by c on the sheared-periodic lattice."""
+    X, Y, Z = x + c[0], y + c[1], z + c[2]
+    if X >= p.nx:
+        X -= p.nx
+        Y -= p.xshift
+    elif X < 0:
+        X += p.nx
+        Y += p.xshift
+    return X + p.nx * ((Y % p.ny) + p.ny * (Z % p.nz))
+
+
+@pytest.mark.parametrize("lat,dims,xshift", [(oracle.D2Q9, (6, 5, 1), 2), (oracle.D2Q9, (5, 7, 1), 0),
+                                             (oracle.D3Q19, (4, 5, 3), 0), (oracle.D3Q19, (3, 4, 5), 1)])
+def test_streaming_is_exact_permutation(oracle_lib, lat, dims, xshift):
+    """A local-equilibrium state is a fixed point of BGK collision, so one update is pure
+    streaming f_i(x + c_i) = f_i(x) (Eq. LBE), here on the sheared-periodic lattice."""
+    rng = np.random.default_rng(3)
+    p = oracle.params(lat, dims, 0.7, xshift=xshift)
+    N = p.nx * p.ny * p.nz
+    rho = 1.0 + 0.05 * rng.standard_normal(N)
+    u = 0.03 * rng.standard_normal((N, 3))
+    if lat == oracle.D2Q9:
+        u[:, 2] = 0.0
+    flags = np.zeros(N, np.uint8)
+    f = oracle.init_eq(p, flags, rho, u)
+    fo = oracle.step(p, flags, f)
+    c, _, _ = oracle.lattice(lat)
+    for n in range(N):
+        x, y, z = n % p.nx, (n // p.nx) % p.ny, n // (p.nx * p.ny)
+        for i in range(len(c)):
+            m = _shifted_neighbour(p, x, y, z, c[i])
+            assert abs(fo[m, i] - f[n, i]) < 1e-15
+
+
+@pytest.mark.parametrize("lat,dims", [(oracle.D2Q9, (8, 6, 1)), (oracle.D3Q19, (5, 4, 6))])
+def test_mass_and_momentum_balance(oracle_lib, lat, dims):
+    """Periodic box: collision and streaming conserve mass; with Guo forcing every fluid
+    node gains exactly F of momentum per step."""
+    rng = np.random.default_rng(5)
+    F = np.array([2e-5, -1e-5, 3e-5 if lat == oracle.D3Q19 else 0.0])
+    p = oracle.params(lat, dims, 0.9, force=F)
+    N = p.nx * p.ny * p.nz
+    flags = np.zeros(N, np.uint8)
+    f = _random_state(p, rng)
+    c, _, _ = oracle.lattice(lat)
+    m0, j0 = f.sum(), (f @ c).sum(0)
+    for _ in range(10):
+        f = oracle.step(p, flags, f)
+    assert abs(f.sum() - m0) / m0 < 1e-14
+    np.testing.assert_allclose((f @ c).sum(0) - j0, 10 * N * F, atol=1e-13)
+
+
+# ---------------------------------------------------------------- boundary rules vs closed forms
+def _plane_couette(lat, bc, qb, qt, H=16, tau=0.8, U=1e-3, steps=None, impulsive=False,
+                   nstep_tstar=None):
+    """Channel periodic in x (and z), walls crossing the links of the first and last fluid
+    row at fractions qb (bottom, at rest) and qt (top, moving with U along x)."""
+    ny = H + 2
+    p = oracle.params(lat, (1, ny, 1), tau, bc=bc)
+    c, _, _ = oracle.lattice(lat)
+    Qn = len(c)
+    flags = np.zeros(ny, np.uint8)
+    flags[0] = flags[-1] = oracle.SOLID
+    q = np.zeros((ny, Qn))
+    uw = np.zeros((ny, Qn, 3))
+    for i in range(Qn):
+        if c[i, 1] == 1:
+            q[1, i] = qb
+        if c[i, 1] == -1:
+            q[H, i] = qt
+            uw[H, i, 0] = U
+    s = oracle.Sim(p, flags, q, uw, uw)
+    return p, s
+
+
+@pytest.mark.parametrize("lat", [oracle.D2Q9, oracle.D3Q19])
+@pytest.mark.parametrize("bc", [oracle.BC_ELIBB_F, oracle.BC_ELIBB_FQ, oracle.BC_BFL])
+@pytest.mark.parametrize("qb,qt", [(0.3, 0.7), (0.1, 0.9), (0.6, 0.05)])
+def test_steady_plane_couette_exact(oracle_lib, lat, bc, qb, qt):
+    """Second-order link-wise rules carry the linear Couette profile exactly at any q
+    (wall positions 1 - qb and H + qt); the moving wall enters through Eq. ME-solid-to-fluid."""
+    H, U = 16, 1e-3
+    p, s = _plane_couette(lat, bc, qb, qt, H=H, U=U)
+    s.run(12000)
+    _, u = s.macros()
+    y = np.arange(1, H + 1) - (1.0 - qb)
+    uth = U * y / ((H + qt) - (1.0 - qb))
+    assert A.rrse(u[1:H + 1, 0], uth) < 1e-10
+    assert np.abs(u[1:H + 1, 1:]).max() < 1e-12
+
+
+def test_half_way_bounce_back_is_first_order_off_half(oracle_lib):
+    """HWBB puts the wall at q = 1/2 whatever q is (Sec. III.A: it degrades for q != 1/2)."""
+    H, U = 16, 1e-3
+    _, s = _plane_couette(oracle.D2Q9, oracle.BC_HWBB, 0.3, 0.7, H=H, U=U)
+    s.run(12000)
+    _, u = s.macros()
+    y = np.arange(1, H + 1) - 0.7
+    assert A.rrse(u[1:H + 1, 0], U * y / (H + 0.7 - 0.7)) > 1e-2
+    y_half = np.arange(1, H + 1) - 0.5
+    assert A.rrse(u[1:H + 1, 0], U * y_half / (H + 0.5 - 0.5)) < 1e-10
+
+
+def _impulsive(bc, q, H, tau=0.8, U=1e-3, tstar=0.05):
+    """Sec. III.A: node rows at y = q + j, walls at 0 and h = H - 1 + 2q."""
+    p, s = _plane_couette(oracle.D2Q9, bc, q, q, H=H, tau=tau, U=U)
+    h = H - 1 + 2 * q
+    nu = (tau - 0.5) / 3.0
+    steps = int(round(tstar * h * h / nu))
+    s.run(steps)
+    _, u = s.macros()
+    uth = A.couette_impulsive(q + np.arange(H), steps, h, U, nu)
+    return A.rrse(u[1:H + 1, 0], uth)
+
+
+@pytest.mark.parametrize("bc", [oracle.BC_ELIBB_F, oracle.BC_ELIBB_FQ, oracle.BC_BFL,
+                                oracle.BC_ELIBB_U, oracle.BC_ELIBB_UQ])
+def test_impulsive_couette_second_order(oracle_lib, bc):
+    """Impulsively started Couette vs the 100-term series (Eq. solution-couette):
+    second-order convergence of rRSE (Sec. III.A)."""
+    e = [_impulsive(bc, 0.3, H) for H in (10, 20, 40)]
+    orders = np.log2(np.array(e[:-1]) / np.array(e[1:]))
+    assert (orders > 1.8).all(), (e, orders)
+    assert e[-1] < 2e-3
+
+
+def test_impulsive_couette_hwbb_first_order(oracle_lib):
+    e = [_impulsive(oracle.BC_HWBB, 0.3, H) for H in (10, 20, 40)]
+    orders = np.log2(np.array(e[:-1]) / np.array(e[1:]))
+    assert (orders < 1.2).all() and (orders > 0.8).all()
+
+
+def test_quadratic_variants_more_accurate(oracle_lib):
+    """Sec. III.A: the quadratic ELIBB variants are generally more accurate."""
+    eF = _impulsive(oracle.BC_ELIBB_F, 0.3, 20)
+    eFQ = _impulsive(oracle.BC_ELIBB_FQ, 0.3, 20)
+    assert eFQ < eF
+
+
+def _cylinders(bc, L, tau=0.8, uin=0.01, tol=1e-9):
+    R1, R2 = 0.25 * L, 0.45 * L
+    cx = cy = L / 2.0
+    om = uin / R1
+    p = oracle.params(oracle.D2Q9, (L, L, 1), tau, bc=bc)
+    shapes = [dict(type=oracle.SHAPE_SPHERE, tag=1, c=(cx, cy, 0), r=(R1, 0, 0), om=(0, 0, om),
+                   om1=(0, 0, om)),
+              dict(type=oracle.SHAPE_SPHERE_OUT, tag=2, c=(cx, cy, 0), r=(R2, 0, 0))]
+    flags, q, uw, uw1, tag = oracle.geometry(p, shapes=shapes)
+    X, Y = np.meshgrid(np.arange(L), np.arange(L))
+    dx, dy = X.ravel() - cx, Y.ravel() - cy
+    r = np.hypot(dx, dy)
+    fl = flags == oracle.FLUID
+    ut = np.zeros(r.size)
+    ut[fl] = A.cylindrical_couette(r[fl], R1, R2, om)
+    rs = np.where(r > 0, r, 1.0)
+    uth = np.stack([-ut * dy / rs, ut * dx / rs, 0 * r], 1)
+    s = oracle.Sim(p, flags, q, uw, uw1, oracle.init_eq(p, flags, None, uth))
+    prev = s.macros()[1]
+    while s.t < 100000:
+        s.run(500)
+        u = s.macros()[1]
+        change = np.sqrt(((u - prev) ** 2).sum() / (u ** 2).sum())
+        prev = u
+        if change < tol:
+            break
+    flink = s.run(1, want_force=True)
+    u = s.macros()[1]
+    err = np.sqrt(((u[fl] - uth[fl]) ** 2).sum() / (uth[fl] ** 2).sum())
+    torque = {}
+    for tg in (1, 2):
+        m = tag == tg
+        rx = np.broadcast_to(dx[:, None], m.shape)[m]
+        ry = np.broadcast_to(dy[:, None], m.shape)[m]
+        fl_ = flink[m]
+        torque[tg] = float((rx * fl_[:, 1] - ry * fl_[:, 0]).sum())
+    nu = (tau - 0.5) / 3.0
+    return err, torque, A.couette_torque(1.0, nu, om, R1, R2)
+
+
+@pytest.mark.parametrize("bc", [oracle.BC_ELIBB_F, oracle.BC_ELIBB_FQ, oracle.BC_BFL])
+def test_cylindrical_couette_convergence_and_torque(oracle_lib, bc):
+    """Circular Couette (Sec. III.B closed form): second-order rRSE; momentum-exchange
+    torques (Eq. force-boundary-node) equal and opposite and equal to 4 pi mu w1 r1^2 r2^2/(r2^2-r1^2)."""
+    res = [_cylinders(bc, L) for L in (32, 64)]
+    e = [r[0] for r in res]
+    assert np.log2(e[0] / e[1]) > 1.8, e
+    for err, tq, T in res:
+        assert tq[1] < 0 < tq[2]
+        assert abs(tq[1] + T) / T < 2e-3
+        assert abs(tq[1] + tq[2]) / T < 1e-3
+
+
+def test_force_balance_body_force_channel(oracle_lib):
+    """Steady body-force channel: the wall force balances the body force (momentum balance)."""
+    H, g = 12, 1e-5
+    for bc, qb, qt in [(oracle.BC_ELIBB_F, 0.3, 0.7), (oracle.BC_ELIBB_FQ, 0.8, 0.2),
+                       (oracle.BC_BFL, 0.25, 0.6)]:
+        ny = H + 2
+        p = oracle.params(oracle.D2Q9, (1, ny, 1), 0.9, bc=bc, force=(g, 0, 0))
+        c, _, _ = oracle.lattice(oracle.D2Q9)
+        flags = np.zeros(ny, np.uint8)
+        flags[0] = flags[-1] = oracle.SOLID
+        q = np.zeros((ny, 9))
+        q[1, c[:, 1] == 1] = qb
+        q[H, c[:, 1] == -1] = qt
+        s = oracle.Sim(p, flags, q)
+        s.run(8000)
+        flink = s.run(1, want_force=True)
+        Fx = flink[..., 0].sum()
+        assert abs(Fx - g * H) / (g * H) < 1e-6
+        # steady profile: parabola between the walls at 1 - qb and H + qt
+        _, u = s.macros()
+        W = (H + qt) - (1 - qb)
+        sy = np.arange(1, H + 1) - (1 - qb)
+        nu = (0.9 - 0.5) / 3
+        assert A.rrse(u[1:H + 1, 0], g * sy * (W - sy) / (2 * nu)) < 2e-2  # BGK wall slip at H = 12
+
+
+def test_velocity_inlet_pressure_outlet_uniform_flow(oracle_lib):
+    """A moving half-way wall at the inlet and the single-node pressure outlet keep the
+    uniform flow u = U, rho = rho0 as their exact steady state."""
+    for lat, dims in [(oracle.D2Q9, (24, 3, 1)), (oracle.D3Q19, (16, 2, 2))]:
+        p = oracle.params(lat, dims, 0.8)
+        N = p.nx * p.ny * p.nz
+        base = np.zeros(N, np.uint8)
+        base_u = np.zeros((N, 3))
+        x = np.arange(N) % p.nx
+        base[x == 0] = oracle.SOLID
+        base_u[x == 0, 0] = 0.02
+        base[x == p.nx - 1] = oracle.OPEN
+        flags, q, uw, uw1, _ = oracle.geometry(p, base, base_u)
+        u0 = np.zeros((N, 3))
+        u0[:, 0] = 0.02
+        s = oracle.Sim(p, flags, q, uw, uw1, oracle.init_eq(p, flags, None, u0))
+        s.run(50)
+        rho, u = s.macros()
+        fl = flags == oracle.FLUID
+        assert np.abs(u[fl, 0] - 0.02).max() < 1e-13
+        assert np.abs(rho[fl] - 1.0).max() < 1e-13
+        # from rest the flow relaxes to the same state (acoustic reflections decay slowly)
+        s = oracle.Sim(p, flags, q, uw, uw1)
+        s.run(12000)
+        rho, u = s.macros()
+        assert np.abs(u[fl, 0] - 0.02).max() < 1e-4
+
+
+# ---------------------------------------------------------------- geometry
+def _bisect(inside, x, c, lo=0.0, hi=1.0, it=200):
+    """Crossing of the segment x - t c with the solid by bisection (brute force)."""
+    assert not inside(x) and inside(x - hi * c)
+    for _ in range(it):
+        mid = 0.5 * (lo + hi)
+        if inside(x - mid * c):
+            hi = mid
+        else:
+            lo = mid
+    return 0.5 * (lo + hi)
+
+
+@pytest.mark.parametrize("kind", ["sphere", "sphere_out", "ellipsoid", "strip"])
+def test_link_q_matches_bisection(oracle_lib, kind):
+    """q is the exact crossing fraction along -c_i (Sec. II.B); flags by brute force."""
+    if kind == "strip":
+        lat, dims = oracle.D2Q9, (52, 84, 1)
+        th = np.arctan2(15.0, 26.0)
+        nrm = np.array([-np.sin(th), np.cos(th), 0.0])
+        per = 84 * nrm[1]
+        shape = dict(type=oracle.SHAPE_STRIP, nrm=nrm, off=40.0, width=40.0, period=per)
+
+        def inside(X):
+            v = nrm @ X - 40.0
+            v = v - per * np.floor(v / per + 0.5)
+            return abs(v) >= 20.0
+        xshift = 30
+    else:
+        lat, dims, xshift = oracle.D3Q19, (20, 18, 16), 0
+        cen = np.array([9.3, 8.6, 7.9])
+        if kind == "sphere":
+            shape = dict(type=oracle.SHAPE_SPHERE, c=cen, r=(5.2, 0, 0))
+
+            def inside(X):
+                return ((X - cen) ** 2).sum() <= 5.2 ** 2
+        elif kind == "sphere_out":
+            shape = dict(type=oracle.SHAPE_SPHERE_OUT, c=cen, r=(7.1, 0, 0))
+
+            def inside(X):
+                return ((X - cen) ** 2).sum() >= 7.1 ** 2
+        else:
+            ax = np.array([6.3, 4.1, 3.7])
+            shape = dict(type=oracle.SHAPE_ELLIPSOID, c=cen, r=ax)
+
+            def inside(X):
+                return (((X - cen) / ax) ** 2).sum() <= 1.0
+    p = oracle.params(lat, dims, 0.8, xshift=xshift)
+    flags, q, _, _, _ = oracle.geometry(p, shapes=[shape])
+    c, _, _ = oracle.lattice(lat)
+    N = p.nx * p.ny * p.nz
+    ncut = 0
+    for n in range(N):
+        X = np.array([n % p.nx, (n // p.nx) % p.ny, n // (p.nx * p.ny)], float)
+        assert flags[n] == (oracle.SOLID if inside(X) else oracle.FLUID)
+        if flags[n] != oracle.FLUID:
+            continue
+        for i in range(1, len(c)):
+            m = _shifted_neighbour(p, int(X[0]), int(X[1]), int(X[2]), -c[i])
+            if flags[m] == oracle.FLUID:
+                continue
+            ncut += 1
+            qb = _bisect(inside, X, c[i].astype(float))
+            assert abs(q[n, i] - qb) < 1e-12, (n, i, q[n, i], qb)
+            assert 0.0 < q[n, i] <= 1.0
+    assert ncut > 20
+
+
+def test_wall_velocity_is_rigid_motion(oracle_lib):
+    """u_w at x_W = x_F - q c_i is V + Omega x (x_W - centre) (Sec. II.E)."""
+    p = oracle.params(oracle.D3Q19, (16, 16, 16), 0.8)
+    cen = np.array([7.7, 8.2, 8.1])
+    V = np.array([0.01, -0.02, 0.005])
+    Om = np.array([0.001, 0.002, -0.003])
+    shape = dict(type=oracle.SHAPE_SPHERE, tag=3, c=cen, r=(4.4, 0, 0), v=V, om=Om, v1=2 * V, om1=Om)
+    flags, q, uw, uw1, tag = oracle.geometry(p, shapes=[shape])
+    c, _, _ = oracle.lattice(oracle.D3Q19)
+    idx = np.argwhere(q > 0)
+    assert len(idx) > 50
+    for n, i in idx:
+        X = np.array([n % 16, (n // 16) % 16, n // 256], float)
+        xw = X - q[n, i] * c[i]
+        np.testing.assert_allclose(uw[n, i], V + np.cross(Om, xw - cen), atol=1e-16)
+        np.testing.assert_allclose(uw1[n, i], 2 * V + np.cross(Om, xw - cen), atol=1e-16)
+        assert tag[n, i] == 3
