@@ -1,0 +1,333 @@
+"""Benchmark: fused D3Q19 stream-collide with the ELIBB single-node boundary rule.
+
+Workload: the sphere-in-duct configuration at full size. It is a D3Q19 BGK
+256 x 128 x 128 duct, tau = 0.7, with a velocity inlet u = 0.02, a pressure
+outlet and a fixed sphere of radius 16 at (64, 64, 64). Populations are
+stored in FP32, shifted by w_i rho0, and the collision runs in FP32.
+
+One step is one fused stream-collide-boundary pass over the grid: a k_step
+launch, replayed from a CUDA graph. The metric is MLUPS counting fluid nodes.
+The roofline fraction divides the algorithmic bytes of a launch by its average
+CUDA-event duration and by the measured HBM copy bandwidth. Each of the two
+population buffers (319 MB) is larger than L2, so no L2 flush is needed.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--dtype f32|f16|bf16|f64]
+Under torchrun each rank runs an independent replica (the path does not
+shard). The ranks meet in barriers only and report the maximum time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DTYPE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+METRIC = "MLUPS (fluid-node lattice updates per second) of the fused D3Q19 stream-collide with the ELIBB boundary rule"
+WORKLOAD = "sphere_duct_d3q19_256x128x128"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="f32", choices=list(DTYPE_BYTES))
+    ap.add_argument("--bc", default="elibb_f")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if len(s) > 4 + k and s[4 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------- helpers
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "lattice.cuh", "kernels.cu"):
+        with open(os.path.join(ROOT, "paper_2009_04604_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(dtype):
+    """DRAM bytes per k_step launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"k_step_d3q19_{dtype}_sphere_duct.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        if d.get("kernel_source_hash") == kernel_source_hash():
+            return float(d["dram_bytes_per_launch_full_size"])
+    except Exception:
+        pass
+    return None
+
+
+def dist_setup(n):
+    if n <= 1 or "RANK" not in os.environ:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    world = int(os.environ["WORLD_SIZE"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    return rank, world, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def algorithmic_bytes(nfluid, np_, nb, nl, Q, s, ls, moving):
+    """Bytes a launch must move: each fluid population read and written once,
+    one flag byte per (padded) node, 16 B per boundary record, q (and u_w) per wall link."""
+    return nfluid * 2 * Q * s + np_ + nb * 16 + nl * ls * (7 if moving else 1)
+
+
+# ---------------------------------------------------------------- the oracle CPU baseline
+def run_oracle(wl, budget_s, min_steps=1, max_steps=None):
+    import oracle
+    kinds = {"sphere": oracle.SHAPE_SPHERE, "sphere_out": oracle.SHAPE_SPHERE_OUT,
+             "ellipsoid": oracle.SHAPE_ELLIPSOID, "strip": oracle.SHAPE_STRIP}
+    shapes = [dict(s, type=kinds[s["type"]]) for s in wl["shapes"]]
+    p = oracle.params(wl["lattice"], wl["dims"], wl["tau"], bc=oracle.BC_ELIBB_F, rho0=wl["rho0"],
+                      force=wl["force"], xshift=wl["xshift"])
+    flags, q, uw, uw1, _ = oracle.geometry(p, wl["base"], wl["base_u"], shapes)
+    f = oracle.init_eq(p, flags)
+    nfluid = int((flags == 0).sum())
+    steps = 0
+    t0 = time.perf_counter()
+    while steps < min_steps or (time.perf_counter() - t0 < budget_s and (max_steps is None or steps < max_steps)):
+        f = oracle.step(p, flags, f, q, uw, uw1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return nfluid * steps / dt / 1e6, steps, dt, nfluid
+
+
+def cores_used():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+# ---------------------------------------------------------------- arms
+def reference_arm(args, rank, dist):
+    from paper_2009_04604_gb300 import workloads as W
+    import oracle
+    if rank != 0:
+        return 0
+    oracle.build()
+    wl = W.sphere_duct()
+    run_oracle(wl, 0.0, min_steps=max(1, min(args.warmup, 1)))  # warm-up
+    # each timed "step" is one full-size oracle step; bounded to about 2 minutes
+    mlups, steps, dt, nfluid = run_oracle(wl, 120.0, min_steps=1, max_steps=max(1, args.steps))
+    line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": steps, "warmup": 1, "ms_per_step": round(dt / steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "lattice": "D3Q19", "tau": 0.7,
+                                             "bc": "elibb_f", "nfluid": nfluid},
+            "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": cores_used(), "kind": "oracle",
+                             "sample": f"{steps} full-size steps of {WORKLOAD} (FP64 oracle, OpenMP)"},
+            "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def ours_arm(args, rank, world, dist):
+    import torch
+    from paper_2009_04604_gb300 import build, lbm
+    from paper_2009_04604_gb300 import workloads as W
+    build.build()
+    dev = torch.cuda.current_device()
+    wl = W.sphere_duct()
+    s = lbm.Simulation(wl["lattice"], wl["dims"], wl["tau"], args.dtype)
+    s.set_options(args.bc, wl["rho0"], wl["force"], wl["xshift"])
+    s.build_geometry(wl["base"], wl["base_u"], wl["shapes"])
+    s.init(wl["rho0"])
+    nfluid, nb, nl = s.counts()
+    N = s.N
+    np_ = (wl["dims"][0] + 31) // 32 * 32 * wl["dims"][1] * wl["dims"][2]
+    stream = s.stream
+    W_ = max(3, args.warmup)
+    s.step(W_)
+    s.synchronize()
+    # ---- device-timed region: K graph-replayed steps, events on the library stream
+    barrier(dist)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        ev0.record(stream)
+        s.step(args.steps)
+        ev1.record(stream)
+        ev1.synchronize()
+    torch.cuda.synchronize()
+    barrier(dist)
+    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(dist, ms)
+    ms_step = ms / args.steps
+    mlups = world * nfluid * args.steps / (ms * 1e-3) / 1e6
+    # ---- roofline of the step kernel
+    peak, peak_kind = measured_peak()
+    s_bytes = DTYPE_BYTES[args.dtype]
+    ls = 8 if args.dtype == "f64" else 4
+    abytes = algorithmic_bytes(nfluid, np_, nb, nl, 19, s_bytes, ls, False)
+    achieved = abytes / (ms_step * 1e-3) / 1e9
+    traffic = profiled_traffic(args.dtype)
+    # ---- end to end through the public API: upload the state from pinned host memory,
+    # then per step lbm_step(1) and a synchronising read of the drag force (24 B)
+    K2 = min(args.steps, 200)
+    f_host = None
+    e2e = None
+    try:
+        f_host = torch.empty((N, 19), dtype=torch.float64).pin_memory()
+        f_host.numpy()[:] = s.get_populations()
+        barrier(dist)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.set_populations(f_host.numpy())
+        for _ in range(K2):
+            s.step(1)
+            s.wall_force(1)
+        s.synchronize()
+        t1 = time.perf_counter()
+        dt = max_over_ranks(dist, t1 - t0)
+        e2e = {"value": round(world * nfluid * K2 / dt / 1e6, 2), "unit": "MLUPS",
+               "h2d_bytes_per_step": int(N * 19 * 8 / K2), "d2h_bytes_per_step": 24,
+               "steps": K2, "note": "per step: lbm_step(1) + lbm_wall_force readback; the initial state "
+                                    "upload (pinned host FP64) is inside the timed region, amortised per step"}
+    except Exception as exc:  # pragma: no cover - reported, not hidden
+        e2e = {"value": None, "unit": "MLUPS", "error": str(exc)[:200]}
+    # ---- oracle on the host cores (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            import oracle
+            oracle.build()
+            mlups_cpu, steps_cpu, dt_cpu, _ = run_oracle(wl, 15.0, min_steps=2)
+            cpu = {"value": round(mlups_cpu, 4), "unit": "MLUPS", "cores": cores_used(), "kind": "oracle",
+                   "sample": f"{steps_cpu} full-size steps of {WORKLOAD} in {dt_cpu:.1f} s (FP64 oracle, OpenMP)"}
+        except Exception as exc:
+            cpu = {"value": None, "unit": "MLUPS", "cores": cores_used(), "kind": "oracle", "error": str(exc)[:200]}
+    _, u = s.macros()
+    finite = bool(torch.isfinite(u).all().item())
+    s.close()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": round(mlups, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": W_, "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": "D3Q19", "dims": list(wl["dims"]), "tau": wl["tau"],
+                   "bc": args.bc, "storage": f"{args.dtype} shifted (f - w rho0)",
+                   "math": "f64" if args.dtype == "f64" else "f32", "nfluid": nfluid, "nodes": N,
+                   "boundary_nodes": nb, "wall_links": nl, "l2": "inputs larger than L2 (2 x "
+                   f"{19 * np_ * s_bytes / 1e6:.0f} MB population buffers); no flush",
+                   "parallelism": f"replicas x{world}", "graph_steps": 32},
+        "mlups_all_nodes": round(world * N * args.steps / (ms * 1e-3) / 1e6, 2),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "peak_source": peak_kind, "algorithmic_bytes_per_launch": int(abytes),
+                     "kernel": "k_step<D3Q19>", "duration_us": round(ms_step * 1e3, 2)},
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "cpu_baseline": cpu,
+        "state_finite": finite,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, dist = dist_setup(args.gpus)
+    try:
+        if args.impl == "reference":
+            return reference_arm(args, rank, dist)
+        return ours_arm(args, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,181 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) lattice Boltzmann library liblbm.so.
+ *
+ * The library advances the lattice Boltzmann equation with BGK collision on
+ * D2Q9 and D3Q19 lattices (Sec. II.A, Eqs. LBE, LB-BGK, Eq2ndOrder of
+ * arXiv:2009.04604) in one fused stream-collide kernel. On boundary nodes the same
+ * kernel applies a link-wise curved-wall Dirichlet rule. The rules are ELIBB-F and
+ * ELIBB-FQ (Sec. II.D), linear BFL (Sec. II.B, Eq. bfl) and half-way bounce-back,
+ * with the moving-wall term of Sec. II.E. Every rule takes its per-link wall
+ * distance q and wall velocity u_w from the geometry. The momentum-exchange wall
+ * force (Sec. II.F) and the total mass are reduced in FP64.
+ *
+ * Conventions for every call:
+ *   - Every call returns an lbm_status (0 = LBM_OK). No call aborts or exits.
+ *     lbm_last_error() gives a message for the last failing call on a handle.
+ *   - Node index n = x + nx*(y + ny*z), with x fastest. D2Q9 uses nz = 1.
+ *     The index space is periodic in every axis. Walls, inlets and outlets are
+ *     nodes flagged non-fluid. Optionally the x axis is sheared-periodic: node
+ *     (x + nx, y + xshift) is node (x, y).
+ *   - Per-link arrays are indexed [n*Q + i]. Link i of node n joins n to
+ *     n - c_i, the node its population i streams from. Directions follow this
+ *     library's own order, which lbm_lattice_info() returns. Opposite
+ *     directions satisfy opp(i) = Q - 1 - i.
+ *   - Host arrays passed in are read during the call and copied. The caller
+ *     keeps ownership. Device buffers passed in (lbm_macros) are caller-owned
+ *     and are written on the handle's stream.
+ *   - The handle owns all device state: populations, flags, boundary records
+ *     and scratch. lbm_step() only enqueues work on the stream. Errors raised
+ *     on the device show up at the next call that synchronises.
+ *   - A handle must not be used by two host threads at the same time.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_sim *lbm_handle;
+
+enum lbm_lattice { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };
+
+/* Storage type of the populations. F64 computes in FP64. The others keep the
+ * shifted value f_i - w_i rho0 in the stated format and compute in FP32. */
+enum lbm_dtype { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2, LBM_BF16 = 3 };
+
+/* Boundary rule on wall links:
+ *   ELIBB_F  fragmented linear single-node rule (Sec. II.D, Eq. linear_broken_method);
+ *   ELIBB_FQ fragmented quadratic rule, which falls back to ELIBB_F for
+ *            q < 0.01 (Sec. II.D, Eq. quadratic_fragmented_method);
+ *   BFL      linear Bouzidi rule (Sec. II.B, Eq. bfl). It falls back to half-way
+ *            bounce-back where the second fluid node along the link is missing;
+ *   HWBB     half-way bounce-back (Sec. II.B). */
+enum lbm_bc { LBM_BC_ELIBB_F = 0, LBM_BC_ELIBB_FQ = 1, LBM_BC_BFL = 2, LBM_BC_HWBB = 3 };
+
+/* Node kinds. A link into an OPEN node gets the single-node pressure rule
+ * f_i = f_i^eq(rho0, u_F) + f^neq_ibar(x_F), the non-equilibrium bounce-back of
+ * Eq. neqbb-s applied at the reference density. */
+enum lbm_node { LBM_FLUID = 0, LBM_SOLID = 1, LBM_OPEN = 2 };
+
+enum lbm_status {
+  LBM_OK = 0,
+  LBM_ERR_ARG = -1,       /* bad argument: null pointer, size, tau <= 1/2, q outside (0,1] */
+  LBM_ERR_CUDA = -2,      /* a CUDA runtime call failed */
+  LBM_ERR_OOM = -3,       /* device allocation failed */
+  LBM_ERR_NONFINITE = -4, /* a reduction found NaN or Inf in the state */
+  LBM_ERR_TIMEOUT = -5,   /* a bounded device wait ran out */
+  LBM_ERR_STATE = -6      /* call out of order, e.g. stepping before set_geometry */
+};
+
+/* Analytic shapes for lbm_build_geometry. A node is solid where the shape's test
+ * holds (ties count as solid). */
+enum lbm_shape_type {
+  LBM_SHAPE_SPHERE = 0,     /* solid inside |x - c| <= r[0] (a circle on D2Q9)            */
+  LBM_SHAPE_SPHERE_OUT = 1, /* solid outside |x - c| >= r[0]                               */
+  LBM_SHAPE_ELLIPSOID = 2,  /* solid inside sum_d ((x - c)_d / r[d])^2 <= 1, axis-aligned  */
+  LBM_SHAPE_STRIP = 3       /* fluid where |v| < width/2, with v = nrm.x - off. When
+                               period > 0, v is first wrapped into [-period/2, period/2) */
+};
+
+typedef struct {
+  int type;                 /* lbm_shape_type */
+  int tag;                  /* force tag 0..7 given to every link the shape cuts */
+  double c[3], r[3];        /* centre; radius r[0] or semi-axes r[0..2] */
+  double nrm[3];            /* strip unit normal */
+  double off, width, period;/* strip parameters */
+  double v[3], om[3];       /* rigid velocity, angular velocity at time t */
+  double v1[3], om1[3];     /* the same at time t+1 (wall population at s = 0) */
+} lbm_shape;
+
+/* Lattice tables in this library's direction order: c[i*3 + d], w[i].
+ * Either output may be NULL. Writes *Q. */
+int lbm_lattice_info(int lattice, int *Q, int *c, double *w);
+
+/* Create a simulation on the current CUDA device. dims = {nx, ny, nz}; nz must
+ * be 1 for D2Q9. tau > 1/2 is the BGK relaxation time, Omega = 1/tau (Eq. LB-BGK).
+ * stream is a cudaStream_t (NULL = legacy default stream). Allocates the two
+ * population buffers and the flags. The state starts uninitialised: call
+ * lbm_set_geometry or lbm_build_geometry, then lbm_init or lbm_set_populations. */
+int lbm_create(int lattice, const int dims[3], double tau, int dtype, void *stream,
+               lbm_handle *out);
+int lbm_destroy(lbm_handle h);
+
+/* Boundary rule (lbm_bc), reference density rho0 (default 1), constant body-force
+ * density F (Guo forcing; NULL = none) and the x-wrap shear (0 = plain periodic). */
+int lbm_set_options(lbm_handle h, int bc, double rho0, const double force[3], int xshift);
+
+/* Explicit geometry from host arrays.
+ *   flags[N]: lbm_node per node.
+ *   q[N*Q]: wall distance of each wall link (a fluid node n with a SOLID node
+ *     n - c_i), as a fraction of |c_i| in (0,1]. NULL means every wall link has q = 1/2.
+ *   uw[N*Q*3], uw1[N*Q*3]: wall velocity at the wall point at t and at t+1.
+ *     NULL uw means walls at rest. NULL uw1 means the same as uw.
+ *   tag[N*Q]: force tag 0..7 of each wall link. NULL means tag 0.
+ * Entries of links that are not wall links are ignored. Returns LBM_ERR_ARG
+ * for a wall link with q outside (0,1] or a tag outside 0..7. */
+int lbm_set_geometry(lbm_handle h, const uint8_t *flags, const double *q, const double *uw,
+                     const double *uw1, const int32_t *tag);
+
+/* Geometry computed on the device from analytic shapes (link-geometry kernel).
+ *   base[N] (host, may be NULL): the caller's nodes (walls, inlet, outlet). A
+ *     fluid base node inside any shape becomes SOLID.
+ *   base_u[N*3] (host, may be NULL): velocity of the SOLID base nodes.
+ * A wall link cut by a base node gets q = 1/2 and that node's velocity, tag 0.
+ * A link cut by a shape gets the exact crossing q, the smallest t in (0,1] at
+ * which x_F - t c_i reaches the shape, and the rigid-motion velocity
+ * v + om x (x_W - c) at the wall point x_W = x_F - q c_i. At most 65536 shapes. */
+int lbm_build_geometry(lbm_handle h, const uint8_t *base, const double *base_u,
+                       const lbm_shape *shapes, int nshapes);
+
+/* Equilibrium start f = f^eq(rho, u) on every fluid node. */
+int lbm_init(lbm_handle h, double rho, const double u[3]);
+
+/* Pre-collision populations at the current time, as host FP64 arrays
+ * f[n*Q + i], unshifted, in this library's direction order. Non-fluid entries are
+ * ignored on set and written as 0 on get. */
+int lbm_set_populations(lbm_handle h, const double *f);
+int lbm_get_populations(lbm_handle h, double *f);
+
+/* Enqueue n fused stream-collide-boundary steps on the handle's stream. The
+ * steps are replayed from a captured CUDA graph. */
+int lbm_step(lbm_handle h, int n);
+
+/* Density rho[N] and Guo-corrected velocity u[N*3] ((sum c f + F/2)/rho, Guo
+ * forcing) of the current state. Both are device FP64 buffers owned by the
+ * caller; either may be NULL. Non-fluid nodes get 0. Asynchronous on the stream. */
+int lbm_macros(lbm_handle h, double *rho, double *u);
+
+/* Momentum-exchange force (Sec. II.F, Eq. force-boundary-node, outgoing
+ * population f*_ibar as in Wen et al.) of the last step. It sums
+ * (c_ibar - u_w) f*_ibar(x_F, t) - (c_i - u_w) f_i(x_F, t+1) over the wall links
+ * with this tag (tag = -1 sums every tag). Accumulated in FP64 in a fixed
+ * order, so the result is deterministic. Synchronises the stream. */
+int lbm_wall_force(lbm_handle h, int tag, double F[3]);
+
+/* Total mass sum of rho over the fluid nodes, in FP64. Deterministic. Synchronises.
+ * Returns LBM_ERR_NONFINITE if the sum is NaN or Inf. */
+int lbm_mass(lbm_handle h, double *m);
+
+/* Read back the geometry the library holds, for checks: flags[N] (lbm_node),
+ * q/uw/uw1/tag per link [N*Q(*3)]. Non-wall links read 0. Any pointer may be NULL. */
+int lbm_get_geometry(lbm_handle h, uint8_t *flags, double *q, double *uw, double *uw1,
+                     int32_t *tag);
+
+/* Counts of the current geometry: fluid nodes, boundary nodes, wall links. */
+int lbm_get_counts(lbm_handle h, int64_t *n_fluid, int64_t *n_boundary, int64_t *n_links);
+
+/* Wait for all work on the handle's stream. */
+int lbm_synchronize(lbm_handle h);
+
+/* Message of the last error on this handle (or of the last failed lbm_create
+ * when h is NULL). The string stays valid until the next call on h. */
+const char *lbm_last_error(lbm_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,493 @@
+// geometry.cu -- link-geometry kernels: node flags, boundary records, q and u_w
+// from analytic shapes, computed on the device (lbm_build_geometry).
+//
+// q of a wall link (x_F, i) is the smallest t in (0,1] at which the segment
+// x_F - t c_i enters a shape (the normalised wall distance along the link,
+// Sec. II.B). u_w is the rigid-body velocity v + om x (x_W - c) at the wall point
+// x_W = x_F - q c_i (Sec. II.E). This file is compiled with -fmad=false. The
+// solid tests then round exactly like the plain FP64 definition, so the flags
+// are reproducible bit for bit.
+//
+// Candidate shapes of a node come from a uniform cell list. Each cell lists, in
+// increasing shape index, every shape whose bounding box padded by 2 lattice
+// units overlaps the cell. Unbounded shapes (sphere-outside, strip) sit in every
+// cell.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "geometry.hpp"
+#include "sim.hpp"
+
+namespace lbm {
+
+struct GeoShape {
+  int type, tag;
+  double c[3], r[3], nrm[3];
+  double off, width, period;
+  double v[3], om[3], v1[3], om1[3];
+};
+
+struct GeoView {
+  View v;
+  int D;
+  const uint8_t *base;     // [N] caller's node kinds (unpadded) or null
+  const double *base_u;    // [N*3] or null
+  const GeoShape *shapes;
+  const int *cell_start;   // [ncell + 1]
+  const int *cell_items;
+  int cs, cnx, cny, cnz;   // cell size and counts
+};
+
+__device__ __forceinline__ int cell_of(const GeoView &g, int x, int y, int z) {
+  const int a = min(x / g.cs, g.cnx - 1), b = min(y / g.cs, g.cny - 1), c = min(z / g.cs, g.cnz - 1);
+  return (c * g.cny + b) * g.cnx + a;
+}
+
+// point inside the solid of the shape (ties count as solid)
+__device__ bool shape_solid(const GeoShape &s, int D, double x0, double x1, double x2) {
+  const double d0 = x0 - s.c[0], d1 = x1 - s.c[1], d2 = D == 3 ? x2 - s.c[2] : 0.0;
+  switch (s.type) {
+    case LBM_SHAPE_SPHERE: return d0 * d0 + d1 * d1 + d2 * d2 <= s.r[0] * s.r[0];
+    case LBM_SHAPE_SPHERE_OUT: return d0 * d0 + d1 * d1 + d2 * d2 >= s.r[0] * s.r[0];
+    case LBM_SHAPE_ELLIPSOID: {
+      const double t0 = d0 / s.r[0], t1 = d1 / s.r[1], t2 = D == 3 ? d2 / s.r[2] : 0.0;
+      return t0 * t0 + t1 * t1 + t2 * t2 <= 1.0;
+    }
+    case LBM_SHAPE_STRIP: {
+      double w = s.nrm[0] * x0 + s.nrm[1] * x1 + (D == 3 ? s.nrm[2] * x2 : 0.0) - s.off;
+      if (s.period > 0.0) w = w - s.period * floor(w / s.period + 0.5);
+      return fabs(w) >= 0.5 * s.width;
+    }
+  }
+  return false;
+}
+
+// smallest t in (0,1] with x - t e on the shape boundary, entering the solid; -1 if none.
+// Quadratic roots in the cancellation-free form.
+__device__ double shape_cross(const GeoShape &s, int D, const double x[3], const int ci[3]) {
+  double d[3], e[3];
+  for (int a = 0; a < 3; ++a) {
+    d[a] = a < D ? x[a] - s.c[a] : 0.0;
+    e[a] = a < D ? (double)ci[a] : 0.0;
+  }
+  if (s.type == LBM_SHAPE_STRIP) {
+    double w = s.nrm[0] * x[0] + s.nrm[1] * x[1] + (D == 3 ? s.nrm[2] * x[2] : 0.0) - s.off;
+    if (s.period > 0.0) w = w - s.period * floor(w / s.period + 0.5);
+    const double a = s.nrm[0] * e[0] + s.nrm[1] * e[1] + s.nrm[2] * e[2];
+    const double h = 0.5 * s.width;
+    double t;
+    if (a > 0.0) t = (w + h) / a;
+    else if (a < 0.0) t = (w - h) / a;
+    else return -1.0;
+    return (t > 0.0 && t <= 1.0) ? t : -1.0;
+  }
+  double R2 = 1.0;
+  if (s.type == LBM_SHAPE_ELLIPSOID) {
+    for (int a = 0; a < D; ++a) { d[a] = d[a] / s.r[a]; e[a] = e[a] / s.r[a]; }
+  } else {
+    R2 = s.r[0] * s.r[0];
+  }
+  const double A = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+  const double B = d[0] * e[0] + d[1] * e[1] + d[2] * e[2];
+  const double C = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] - R2;
+  const double disc = B * B - A * C;
+  if (disc < 0.0) return -1.0;
+  const double sq = sqrt(disc);
+  double t;
+  if (s.type != LBM_SHAPE_SPHERE_OUT) {
+    if (C <= 0.0 || B <= 0.0) return -1.0;
+    t = C / (B + sq);
+  } else {
+    if (C >= 0.0) return -1.0;
+    t = (B >= 0.0) ? (B + sq) / A : C / (B - sq);
+  }
+  return (t > 0.0 && t <= 1.0) ? t : -1.0;
+}
+
+template <class L>
+__device__ __forceinline__ void dir(int i, int c[3]) { c[0] = L::cx(i); c[1] = L::cy(i); c[2] = L::cz(i); }
+
+// 1. node kinds: the caller's base flags, turned SOLID inside any shape
+__global__ void k_geo_flags(const GeoView g, uint8_t *__restrict__ flags) {
+  const View &v = g.v;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= v.np) return;
+  const int x = (int)(n % v.nxp), y = (int)((n / v.nxp) % v.ny), z = (int)(n / ((long long)v.nxp * v.ny));
+  if (x >= v.nx) { flags[n] = K_PAD; return; }
+  const long long hn = ((long long)z * v.ny + y) * v.nx + x;
+  uint8_t k = g.base ? g.base[hn] : (uint8_t)K_FLUID;
+  if (k == K_FLUID) {
+    const int cell = cell_of(g, x, y, z);
+    for (int j = g.cell_start[cell]; j < g.cell_start[cell + 1]; ++j)
+      if (shape_solid(g.shapes[g.cell_items[j]], g.D, (double)x, (double)y, (double)z)) { k = K_SOLID; break; }
+  }
+  flags[n] = k;
+}
+
+// 2. cut/open masks, boundary bit, and per-chunk counts of records and wall links
+template <class L>
+__global__ void k_geo_count(const GeoView g, uint8_t *__restrict__ flags, uint32_t *__restrict__ crec,
+                            uint32_t *__restrict__ clink) {
+  const View &v = g.v;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= v.np) return;  // np is a multiple of 32: whole warps leave together
+  const int x = (int)(n % v.nxp), y = (int)((n / v.nxp) % v.ny), z = (int)(n / ((long long)v.nxp * v.ny));
+  uint32_t cut = 0, open = 0;
+  const uint8_t k = flags[n] & 3;
+  if (k == K_FLUID) {
+    Nbr nb;
+    nb.init(v, x, y, z);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      if (L::cx(i) == 0 && L::cy(i) == 0 && L::cz(i) == 0) continue;
+      const uint8_t km = flags[n + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))] & 3;
+      if (km == K_SOLID) cut |= 1u << i;
+      else if (km == K_OPEN) open |= 1u << i;
+    }
+  }
+  const bool isb = (cut | open) != 0;
+  const uint32_t bal = __ballot_sync(0xffffffffu, isb);
+  uint32_t nl = __popc(cut);
+  for (int o = 16; o > 0; o >>= 1) nl += __shfl_down_sync(0xffffffffu, nl, o);
+  if ((threadIdx.x & 31) == 0) {
+    crec[n >> 5] = __popc(bal);
+    clink[n >> 5] = nl;
+  }
+  __syncwarp();
+  if (isb) flags[n] = k | F_BOUNDARY;
+}
+
+// 3. exclusive scan of per-chunk counts (three launches: blocks, block totals, add)
+__global__ void k_scan_block(uint32_t *__restrict__ a, long long n, uint32_t *__restrict__ tot) {
+  __shared__ uint32_t ws[32];
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t x = i < n ? a[i] : 0u;
+  uint32_t s = x;  // inclusive warp scan
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) >= o) s += y;
+  }
+  if ((threadIdx.x & 31) == 31) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    uint32_t t = ws[threadIdx.x];
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (threadIdx.x >= o) t += y;
+    }
+    ws[threadIdx.x] = t;
+  }
+  __syncthreads();
+  const uint32_t warp_off = (threadIdx.x >> 5) ? ws[(threadIdx.x >> 5) - 1] : 0u;
+  if (i < n) a[i] = warp_off + s - x;
+  if (threadIdx.x == blockDim.x - 1) tot[blockIdx.x] = warp_off + s;
+}
+
+__global__ void k_scan_totals(uint32_t *__restrict__ tot, long long nblk, uint32_t *__restrict__ total) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  uint32_t run = 0;
+  for (long long b = 0; b < nblk; ++b) {
+    const uint32_t t = tot[b];
+    tot[b] = run;
+    run += t;
+  }
+  *total = run;
+}
+
+__global__ void k_scan_add(uint32_t *__restrict__ a, long long n, const uint32_t *__restrict__ tot) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] += tot[blockIdx.x];
+}
+
+// 4. records and per-link q, u_w(t), u_w(t+1), tag
+template <class L, typename LT>
+__global__ void k_geo_fill(const GeoView g, const uint32_t *__restrict__ cbase,
+                           const uint32_t *__restrict__ lbase, Rec *__restrict__ rec,
+                           uint32_t *__restrict__ rnode, LT *__restrict__ lq, LT *__restrict__ luw,
+                           LT *__restrict__ luw1, uint8_t *__restrict__ ltag) {
+  const View &v = g.v;
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= v.np) return;  // whole warps
+  const int x = (int)(n % v.nxp), y = (int)((n / v.nxp) % v.ny), z = (int)(n / ((long long)v.nxp * v.ny));
+  const uint8_t fl = v.flags[n];
+  const bool isb = (fl & F_BOUNDARY) != 0;
+  const uint32_t bal = __ballot_sync(0xffffffffu, isb);
+  Nbr nb;
+  nb.init(v, x, y, z);
+  Rec r = {0u, 0u, 0u, 0u};
+  if (isb) {
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      if (L::cx(i) == 0 && L::cy(i) == 0 && L::cz(i) == 0) continue;
+      const uint8_t km = v.flags[n + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))] & 3;
+      if (km == K_SOLID) r.cut |= 1u << i;
+      else if (km == K_OPEN) r.open |= 1u << i;
+      else continue;
+      if ((v.flags[n + nb.at(L::cx(i), L::cy(i), L::cz(i))] & 3) == K_FLUID) r.ffok |= 1u << i;
+    }
+  }
+  // exclusive warp scan of the wall-link counts gives this node's first link
+  const uint32_t cnt = __popc(r.cut);
+  uint32_t s = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) >= o) s += t;
+  }
+  if (!isb) return;
+  const uint32_t lt = (1u << (threadIdx.x & 31)) - 1u;
+  const uint32_t rid = cbase[n >> 5] + __popc(bal & lt);
+  r.link0 = lbase[n >> 5] + s - cnt;
+  rec[rid] = r;
+  rnode[rid] = (uint32_t)n;
+  const double X[3] = {(double)x, (double)y, (double)z};
+  const int cell = cell_of(g, x, y, z);
+  uint32_t li = r.link0;
+  for (int i = 0; i < L::Q; ++i) {
+    if (!(r.cut & (1u << i))) continue;
+    int c[3];
+    dir<L>(i, c);
+    const long long m = n + nb.at(-c[0], -c[1], -c[2]);
+    double qq = 0.5, u0[3] = {0.0, 0.0, 0.0}, u1[3] = {0.0, 0.0, 0.0};
+    int tg = 0;
+    // the neighbour's kind in the caller's base flags decides who cut the link
+    const int mx = (int)(m % v.nxp), my = (int)((m / v.nxp) % v.ny), mz = (int)(m / ((long long)v.nxp * v.ny));
+    const long long hm = ((long long)mz * v.ny + my) * v.nx + mx;
+    const uint8_t bk = g.base ? g.base[hm] : (uint8_t)K_FLUID;
+    if (bk != K_FLUID) {
+      if (g.base_u && bk == K_SOLID)
+        for (int a = 0; a < 3; ++a) { u0[a] = g.base_u[hm * 3 + a]; u1[a] = u0[a]; }
+    } else {
+      double best = 2.0;
+      int kb = -1;
+      for (int j = g.cell_start[cell]; j < g.cell_start[cell + 1]; ++j) {
+        const int k = g.cell_items[j];
+        const double t = shape_cross(g.shapes[k], g.D, X, c);
+        if (t > 0.0 && t < best) { best = t; kb = k; }
+      }
+      if (kb < 0) {
+        // no root (rounding at a tangent): the wall sits on the solid node
+        best = 1.0;
+        for (int j = g.cell_start[cell]; j < g.cell_start[cell + 1]; ++j) {
+          const int k = g.cell_items[j];
+          if (shape_solid(g.shapes[k], g.D, X[0] - c[0], X[1] - c[1], X[2] - c[2])) { kb = k; break; }
+        }
+      }
+      qq = best;
+      if (kb >= 0) {
+        const GeoShape &sh = g.shapes[kb];
+        double rr[3];
+        for (int a = 0; a < 3; ++a) rr[a] = a < g.D ? X[a] - qq * c[a] - sh.c[a] : 0.0;
+        u0[0] = sh.v[0] + sh.om[1] * rr[2] - sh.om[2] * rr[1];
+        u0[1] = sh.v[1] + sh.om[2] * rr[0] - sh.om[0] * rr[2];
+        u0[2] = sh.v[2] + sh.om[0] * rr[1] - sh.om[1] * rr[0];
+        u1[0] = sh.v1[0] + sh.om1[1] * rr[2] - sh.om1[2] * rr[1];
+        u1[1] = sh.v1[1] + sh.om1[2] * rr[0] - sh.om1[0] * rr[2];
+        u1[2] = sh.v1[2] + sh.om1[0] * rr[1] - sh.om1[1] * rr[0];
+        if (g.D == 2) { u0[2] = 0.0; u1[2] = 0.0; }
+        tg = sh.tag;
+      }
+    }
+    lq[li] = (LT)qq;
+    ltag[li] = (uint8_t)tg;
+    if (luw) for (int a = 0; a < 3; ++a) { luw[3 * li + a] = (LT)u0[a]; luw1[3 * li + a] = (LT)u1[a]; }
+    ++li;
+  }
+}
+
+}  // namespace lbm
+
+using namespace lbm;
+
+#define GEO_CUDA(call)                                                                          \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess) {                                                                    \
+      rc = lbm_fail(h, e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,            \
+                    std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+      goto done;                                                                                \
+    }                                                                                           \
+  } while (0)
+
+static void shape_box(const lbm_shape &s, int D, double lo[3], double hi[3], bool &bounded) {
+  bounded = s.type == LBM_SHAPE_SPHERE || s.type == LBM_SHAPE_ELLIPSOID;
+  for (int a = 0; a < 3; ++a) {
+    const double r = s.type == LBM_SHAPE_ELLIPSOID ? s.r[a] : s.r[0];
+    lo[a] = (a < D) ? s.c[a] - r - 2.0 : -1e300;
+    hi[a] = (a < D) ? s.c[a] + r + 2.0 : 1e300;
+  }
+}
+
+static void exclusive_scan(uint32_t *a, long long n, uint32_t *tot, uint32_t *total, cudaStream_t st) {
+  const long long nblk = (n + 1023) / 1024;
+  k_scan_block<<<(unsigned)nblk, 1024, 0, st>>>(a, n, tot);
+  k_scan_totals<<<1, 1, 0, st>>>(tot, nblk, total);
+  k_scan_add<<<(unsigned)nblk, 1024, 0, st>>>(a, n, tot);
+}
+
+extern "C" int lbm_build_geometry(lbm_handle h, const uint8_t *base, const double *base_u,
+                                  const lbm_shape *shapes, int nshapes) {
+  if (!h) return lbm_fail(nullptr, LBM_ERR_ARG, "null handle");
+  if (nshapes < 0 || nshapes > 65536 || (nshapes > 0 && !shapes))
+    return lbm_fail(h, LBM_ERR_ARG, "bad shape list");
+  const int D = h->lattice == LBM_D2Q9 ? 2 : 3;
+  for (int k = 0; k < nshapes; ++k) {
+    const lbm_shape &s = shapes[k];
+    if (s.type < LBM_SHAPE_SPHERE || s.type > LBM_SHAPE_STRIP) return lbm_fail(h, LBM_ERR_ARG, "unknown shape type");
+    if (s.tag < 0 || s.tag > 7) return lbm_fail(h, LBM_ERR_ARG, "shape tags must be 0..7");
+    if (s.type == LBM_SHAPE_ELLIPSOID)
+      for (int a = 0; a < D; ++a) if (!(s.r[a] > 0.0)) return lbm_fail(h, LBM_ERR_ARG, "ellipsoid axes must be positive");
+    if (s.type == LBM_SHAPE_STRIP && !(s.width > 0.0)) return lbm_fail(h, LBM_ERR_ARG, "strip width must be positive");
+  }
+  if (base)
+    for (long long n = 0; n < h->N; ++n)
+      if (base[n] > LBM_OPEN) return lbm_fail(h, LBM_ERR_ARG, "base flags must be 0, 1 or 2");
+
+  // ---- cell list on the host
+  const int cs = 8;
+  const int cnx = (h->nx + cs - 1) / cs, cny = (h->ny + cs - 1) / cs, cnz = (h->nz + cs - 1) / cs;
+  const long long ncell = (long long)cnx * cny * cnz;
+  std::vector<std::vector<int>> lists(ncell);
+  for (int k = 0; k < nshapes; ++k) {
+    double lo[3], hi[3];
+    bool bounded;
+    shape_box(shapes[k], D, lo, hi, bounded);
+    int a0[3], a1[3];
+    const int cn[3] = {cnx, cny, cnz};
+    for (int a = 0; a < 3; ++a) {
+      if (!bounded || a >= D) { a0[a] = 0; a1[a] = cn[a] - 1; continue; }
+      a0[a] = std::max(0, (int)std::floor(lo[a] / cs));
+      a1[a] = std::min(cn[a] - 1, (int)std::floor(hi[a] / cs));
+    }
+    for (int cz = a0[2]; cz <= a1[2]; ++cz)
+      for (int cy = a0[1]; cy <= a1[1]; ++cy)
+        for (int cx = a0[0]; cx <= a1[0]; ++cx) lists[((long long)cz * cny + cy) * cnx + cx].push_back(k);
+  }
+  std::vector<int> cstart(ncell + 1, 0), items;
+  for (long long c = 0; c < ncell; ++c) {
+    cstart[c] = (int)items.size();
+    items.insert(items.end(), lists[c].begin(), lists[c].end());
+  }
+  cstart[ncell] = (int)items.size();
+  bool moving = false;
+  std::vector<GeoShape> gs(nshapes);
+  for (int k = 0; k < nshapes; ++k) {
+    const lbm_shape &s = shapes[k];
+    GeoShape &o = gs[k];
+    o.type = s.type; o.tag = s.tag;
+    for (int a = 0; a < 3; ++a) {
+      o.c[a] = s.c[a]; o.r[a] = s.r[a]; o.nrm[a] = s.nrm[a];
+      o.v[a] = s.v[a]; o.om[a] = s.om[a]; o.v1[a] = s.v1[a]; o.om1[a] = s.om1[a];
+      if (s.v[a] != 0.0 || s.om[a] != 0.0 || s.v1[a] != 0.0 || s.om1[a] != 0.0) moving = true;
+    }
+    o.off = s.off; o.width = s.width; o.period = s.period;
+  }
+  if (base && base_u)
+    for (long long n = 0; n < h->N && !moving; ++n)
+      if (base[n] == LBM_SOLID && (base_u[3 * n] != 0.0 || base_u[3 * n + 1] != 0.0 || base_u[3 * n + 2] != 0.0))
+        moving = true;
+
+  int rc = LBM_OK;
+  uint8_t *d_base = nullptr;
+  double *d_base_u = nullptr;
+  GeoShape *d_shapes = nullptr;
+  int *d_cstart = nullptr, *d_items = nullptr;
+  uint32_t *crec = nullptr, *clink = nullptr, *tot = nullptr, *totals = nullptr;
+  uint32_t htot[2] = {0u, 0u};
+  const long long nchunk = h->np / 32;
+  const long long nblk = (nchunk + 1023) / 1024;
+  GeoView g;
+  cudaStream_t st = h->stream;
+  h->drop_graphs();
+  h->free_geometry();
+  h->geom_ok = false;
+  if (base) {
+    GEO_CUDA(cudaMalloc(&d_base, h->N));
+    GEO_CUDA(cudaMemcpyAsync(d_base, base, h->N, cudaMemcpyHostToDevice, st));
+  }
+  if (base && base_u) {
+    GEO_CUDA(cudaMalloc(&d_base_u, h->N * 3 * sizeof(double)));
+    GEO_CUDA(cudaMemcpyAsync(d_base_u, base_u, h->N * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  GEO_CUDA(cudaMalloc(&d_shapes, std::max(1, nshapes) * sizeof(GeoShape)));
+  if (nshapes) GEO_CUDA(cudaMemcpyAsync(d_shapes, gs.data(), nshapes * sizeof(GeoShape), cudaMemcpyHostToDevice, st));
+  GEO_CUDA(cudaMalloc(&d_cstart, (ncell + 1) * sizeof(int)));
+  GEO_CUDA(cudaMemcpyAsync(d_cstart, cstart.data(), (ncell + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+  GEO_CUDA(cudaMalloc(&d_items, std::max<size_t>(1, items.size()) * sizeof(int)));
+  if (!items.empty())
+    GEO_CUDA(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  GEO_CUDA(cudaMalloc(&crec, (nchunk + 1) * sizeof(uint32_t)));
+  GEO_CUDA(cudaMalloc(&clink, (nchunk + 1) * sizeof(uint32_t)));
+  GEO_CUDA(cudaMalloc(&tot, (nblk + 1) * sizeof(uint32_t)));
+  GEO_CUDA(cudaMalloc(&totals, 2 * sizeof(uint32_t)));
+
+  g.v = h->view();
+  g.D = D;
+  g.base = d_base;
+  g.base_u = d_base_u;
+  g.shapes = d_shapes;
+  g.cell_start = d_cstart;
+  g.cell_items = d_items;
+  g.cs = cs; g.cnx = cnx; g.cny = cny; g.cnz = cnz;
+  {
+    const unsigned blocks = (unsigned)((h->np + 255) / 256);
+    k_geo_flags<<<blocks, 256, 0, st>>>(g, h->flags);
+    if (h->lattice == LBM_D2Q9) k_geo_count<D2Q9><<<blocks, 256, 0, st>>>(g, h->flags, crec, clink);
+    else k_geo_count<D3Q19><<<blocks, 256, 0, st>>>(g, h->flags, crec, clink);
+    GEO_CUDA(cudaGetLastError());
+    exclusive_scan(crec, nchunk, tot, totals, st);
+    exclusive_scan(clink, nchunk, tot, totals + 1, st);
+    GEO_CUDA(cudaGetLastError());
+    GEO_CUDA(cudaMemcpyAsync(htot, totals, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    GEO_CUDA(cudaStreamSynchronize(st));
+    // cbase: records before each chunk, plus the total at the end
+    GEO_CUDA(cudaMemcpyAsync(h->cbase, crec, nchunk * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+    GEO_CUDA(cudaMemcpyAsync(h->cbase + nchunk, &totals[0], sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+    h->nb = htot[0];
+    h->nl = htot[1];
+    h->has_uw = moving ? 1 : 0;
+    const size_t ls = h->link_size();
+    if (h->nb) {
+      GEO_CUDA(cudaMalloc(&h->rec, h->nb * sizeof(Rec)));
+      GEO_CUDA(cudaMalloc(&h->rnode, h->nb * sizeof(uint32_t)));
+    }
+    if (h->nl) {
+      GEO_CUDA(cudaMalloc(&h->lq, h->nl * ls));
+      GEO_CUDA(cudaMalloc(&h->ltag, h->nl));
+      if (moving) {
+        GEO_CUDA(cudaMalloc(&h->luw, h->nl * 3 * ls));
+        GEO_CUDA(cudaMalloc(&h->luw1, h->nl * 3 * ls));
+      }
+    }
+    g.v = h->view();
+    if (h->nb) {
+      if (h->lattice == LBM_D2Q9) {
+        if (ls == 8) k_geo_fill<D2Q9, double><<<blocks, 256, 0, st>>>(g, crec, clink, h->rec, h->rnode, (double *)h->lq, (double *)h->luw, (double *)h->luw1, h->ltag);
+        else k_geo_fill<D2Q9, float><<<blocks, 256, 0, st>>>(g, crec, clink, h->rec, h->rnode, (float *)h->lq, (float *)h->luw, (float *)h->luw1, h->ltag);
+      } else {
+        if (ls == 8) k_geo_fill<D3Q19, double><<<blocks, 256, 0, st>>>(g, crec, clink, h->rec, h->rnode, (double *)h->lq, (double *)h->luw, (double *)h->luw1, h->ltag);
+        else k_geo_fill<D3Q19, float><<<blocks, 256, 0, st>>>(g, crec, clink, h->rec, h->rnode, (float *)h->lq, (float *)h->luw, (float *)h->luw1, h->ltag);
+      }
+      GEO_CUDA(cudaGetLastError());
+    }
+    // fluid node count
+    {
+      std::vector<uint8_t> fl(h->np);
+      GEO_CUDA(cudaMemcpyAsync(fl.data(), h->flags, h->np, cudaMemcpyDeviceToHost, st));
+      GEO_CUDA(cudaStreamSynchronize(st));
+      long long nf = 0;
+      for (long long n = 0; n < h->np; ++n) nf += (fl[n] & 3) == K_FLUID;
+      h->nfluid = nf;
+    }
+    h->geom_ok = true;
+  }
+done:
+  cudaStreamSynchronize(st);
+  cudaFree(d_base); cudaFree(d_base_u); cudaFree(d_shapes); cudaFree(d_cstart); cudaFree(d_items);
+  cudaFree(crec); cudaFree(clink); cudaFree(tot); cudaFree(totals);
+  return rc;
+}

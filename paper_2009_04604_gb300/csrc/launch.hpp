@@ -1,0 +1,30 @@
+// launch.hpp -- host-side entry points of the kernels (one per kernel family),
+// dispatched on lattice and storage type.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lattice.cuh"
+
+namespace lbm {
+
+struct Launch {
+  dim3 grid, block;
+  cudaStream_t stream;
+};
+
+// lattice: 0 D2Q9, 1 D3Q19; dtype: 0 F64, 1 F32, 2 F16, 3 BF16
+cudaError_t launch_step(int lattice, int dtype, const View &v, const void *fin, void *fout,
+                        const Launch &l);
+cudaError_t launch_init(int lattice, int dtype, const View &v, void *fout, double rho, double ux,
+                        double uy, double uz, const Launch &l);
+cudaError_t launch_set_pop(int lattice, int dtype, const View &v, void *fout, const double *fh,
+                           const Launch &l);
+cudaError_t launch_read(int lattice, int dtype, const View &v, const void *fin, double *fh,
+                        double *rho, double *u, double *mass_part, const Launch &l);
+cudaError_t launch_force(int lattice, int dtype, const View &v, const void *cur, long long nb,
+                         int tag, double *part, const Launch &l);
+cudaError_t launch_reduce_final(const double *part, long long nblocks, int ncomp, double *out,
+                                cudaStream_t s);
+
+}  // namespace lbm

@@ -1,0 +1,435 @@
+// runtime.cu -- host runtime of liblbm: the C ABI of include/lbm.h.
+//
+// Owns the device state of a simulation: the two population buffers (A-B
+// pull), node flags, boundary records and per-link wall data, and the scratch
+// for the FP64 reductions. It builds boundary records from explicit host
+// geometry and captures the step loop in CUDA graphs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "geometry.hpp"
+#include "launch.hpp"
+#include "sim.hpp"
+
+using namespace lbm;
+
+static std::string g_create_error;
+
+int lbm_fail(lbm_sim *h, int code, const std::string &msg) {
+  if (h) h->err = msg; else g_create_error = msg;
+  return code;
+}
+
+#define LBM_CUDA(h, call)                                                                        \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      return lbm_fail((h), e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,         \
+                      std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+  } while (0)
+
+// ---------------------------------------------------------------- lattice info
+template <class L>
+static void fill_info(int *c, double *w) {
+  for (int i = 0; i < L::Q; ++i) {
+    if (c) { c[i * 3] = L::cx(i); c[i * 3 + 1] = L::cy(i); c[i * 3 + 2] = L::cz(i); }
+    if (w) w[i] = weight<L>(i);
+  }
+}
+
+extern "C" int lbm_lattice_info(int lattice, int *Q, int *c, double *w) {
+  if (lattice == LBM_D2Q9) { if (Q) *Q = 9; fill_info<D2Q9>(c, w); return LBM_OK; }
+  if (lattice == LBM_D3Q19) { if (Q) *Q = 19; fill_info<D3Q19>(c, w); return LBM_OK; }
+  return lbm_fail(nullptr, LBM_ERR_ARG, "unknown lattice");
+}
+
+void lbm_sim::lattice_c(int i, int &x, int &y, int &z) const {
+  if (lattice == LBM_D2Q9) { x = D2Q9::cx(i); y = D2Q9::cy(i); z = 0; }
+  else { x = D3Q19::cx(i); y = D3Q19::cy(i); z = D3Q19::cz(i); }
+}
+
+double lbm_sim::lattice_w(int i) const {
+  return lattice == LBM_D2Q9 ? weight<D2Q9>(i) : weight<D3Q19>(i);
+}
+
+size_t lbm_sim::elem_size() const {
+  return dtype == LBM_F64 ? 8 : (dtype == LBM_F32 ? 4 : 2);
+}
+
+size_t lbm_sim::link_size() const { return dtype == LBM_F64 ? 8 : 4; }
+
+// ---------------------------------------------------------------- create / destroy
+extern "C" int lbm_create(int lattice, const int dims[3], double tau, int dtype, void *stream,
+                          lbm_handle *out) {
+  if (!out || !dims) return lbm_fail(nullptr, LBM_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19) return lbm_fail(nullptr, LBM_ERR_ARG, "unknown lattice");
+  if (dtype < LBM_F64 || dtype > LBM_BF16) return lbm_fail(nullptr, LBM_ERR_ARG, "unknown dtype");
+  if (!(tau > 0.5)) return lbm_fail(nullptr, LBM_ERR_ARG, "tau must exceed 1/2");
+  if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1) return lbm_fail(nullptr, LBM_ERR_ARG, "dims must be positive");
+  if (lattice == LBM_D2Q9 && dims[2] != 1) return lbm_fail(nullptr, LBM_ERR_ARG, "D2Q9 needs nz = 1");
+  const long long nxp = (dims[0] + 31) / 32 * 32;
+  const long long np = nxp * dims[1] * (long long)dims[2];
+  if (np >= (1LL << 32)) return lbm_fail(nullptr, LBM_ERR_ARG, "grid too large (2^32 padded nodes)");
+  lbm_sim *h = new lbm_sim();
+  h->lattice = lattice;
+  h->Q = lattice == LBM_D2Q9 ? 9 : 19;
+  h->dtype = dtype;
+  h->nx = dims[0]; h->ny = dims[1]; h->nz = dims[2];
+  h->nxp = (int)nxp;
+  h->np = np;
+  h->N = (long long)dims[0] * dims[1] * dims[2];
+  h->tau = tau;
+  if (stream) {
+    h->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete h; return lbm_fail(nullptr, LBM_ERR_CUDA, cudaGetErrorString(e)); }
+    h->own_stream = true;
+  }
+  const size_t bytes = (size_t)h->Q * np * h->elem_size();
+  cudaError_t e = cudaMalloc(&h->f[0], bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->f[1], bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->flags, np);
+  if (e == cudaSuccess) e = cudaMalloc(&h->cbase, (np / 32 + 1) * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->dres, 8 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->flags, K_PAD, np, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->f[0], 0, bytes, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->f[1], 0, bytes, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    std::string msg = std::string("allocation: ") + cudaGetErrorString(e);
+    lbm_destroy(h);
+    return lbm_fail(nullptr, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, msg);
+  }
+  h->tune_default();
+  *out = h;
+  return LBM_OK;
+}
+
+void lbm_sim::free_geometry() {
+  cudaFree(rec); cudaFree(rnode); cudaFree(lq); cudaFree(luw); cudaFree(luw1); cudaFree(ltag);
+  rec = nullptr; rnode = nullptr; lq = nullptr; luw = nullptr; luw1 = nullptr; ltag = nullptr;
+  nb = nl = 0;
+  has_uw = 0;
+}
+
+void lbm_sim::drop_graphs() {
+  for (int k = 0; k < 2; ++k)
+    if (graph[k]) { cudaGraphExecDestroy(graph[k]); graph[k] = nullptr; }
+}
+
+extern "C" int lbm_destroy(lbm_handle h) {
+  if (!h) return LBM_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  h->drop_graphs();
+  h->free_geometry();
+  cudaFree(h->f[0]); cudaFree(h->f[1]); cudaFree(h->flags); cudaFree(h->cbase);
+  cudaFree(h->dres); cudaFree(h->scratch);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return LBM_OK;
+}
+
+extern "C" const char *lbm_last_error(lbm_handle h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+extern "C" int lbm_synchronize(lbm_handle h) {
+  if (!h) return lbm_fail(nullptr, LBM_ERR_ARG, "null handle");
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+extern "C" int lbm_set_options(lbm_handle h, int bc, double rho0, const double force[3], int xshift) {
+  if (!h) return lbm_fail(nullptr, LBM_ERR_ARG, "null handle");
+  if (bc < LBM_BC_ELIBB_F || bc > LBM_BC_HWBB) return lbm_fail(h, LBM_ERR_ARG, "unknown boundary rule");
+  if (!(rho0 > 0.0) || !std::isfinite(rho0)) return lbm_fail(h, LBM_ERR_ARG, "rho0 must be positive");
+  if (h->geom_ok && h->state_ok && rho0 != h->rho0)
+    return lbm_fail(h, LBM_ERR_STATE, "rho0 changes the stored shift: set it before the state");
+  h->bc = bc;
+  h->rho0 = rho0;
+  h->has_force = 0;
+  for (int a = 0; a < 3; ++a) {
+    h->F[a] = force ? force[a] : 0.0;
+    if (h->F[a] != 0.0) h->has_force = 1;
+  }
+  if (h->lattice == LBM_D2Q9) { h->F[2] = 0.0; }
+  h->xshift = xshift;
+  h->drop_graphs();
+  return LBM_OK;
+}
+
+// ---------------------------------------------------------------- kernel view, launch shapes
+View lbm_sim::view() const {
+  View v;
+  v.nx = nx; v.ny = ny; v.nz = nz; v.nxp = nxp; v.np = np;
+  v.xshift = xshift; v.bc = bc;
+  v.omega = 1.0 / tau; v.rho0 = rho0; v.qcut = qcut;
+  for (int a = 0; a < 3; ++a) v.F[a] = F[a];
+  v.has_force = has_force; v.has_uw = has_uw;
+  v.flags = flags; v.cbase = cbase; v.rec = rec; v.rnode = rnode;
+  v.lq = lq; v.luw = luw; v.luw1 = luw1; v.ltag = ltag;
+  return v;
+}
+
+// Launch shape: bx (multiple of 32 dividing nxp) by by rows.
+Launch lbm_sim::shape(int bx, int by) const {
+  Launch l;
+  l.block = dim3(bx, by, 1);
+  l.grid = dim3(nxp / bx, (ny + by - 1) / by, nz);
+  l.stream = stream;
+  return l;
+}
+
+void lbm_sim::tune_default() {
+  // widest power-of-two multiple of 32 (<= 128) that divides the padded row
+  int bx = 32;
+  while (bx < 128 && nxp % (bx * 2) == 0) bx *= 2;
+  step_bx = bx;
+  step_by = std::max(1, 256 / bx);
+}
+
+Launch lbm_sim::step_shape() const { return shape(step_bx, step_by); }
+Launch lbm_sim::aux_shape() const { return shape(32, 8); }
+
+// ---------------------------------------------------------------- scratch
+int lbm_sim::ensure_scratch(long long doubles) {
+  if (doubles <= scratch_len) return LBM_OK;
+  cudaFree(scratch);
+  scratch = nullptr;
+  scratch_len = 0;
+  LBM_CUDA(this, cudaMalloc(&scratch, doubles * sizeof(double)));
+  scratch_len = doubles;
+  return LBM_OK;
+}
+
+// ---------------------------------------------------------------- state
+extern "C" int lbm_init(lbm_handle h, double rho, const double u[3]) {
+  if (!h) return lbm_fail(nullptr, LBM_ERR_ARG, "null handle");
+  if (!h->geom_ok) return lbm_fail(h, LBM_ERR_STATE, "set the geometry first");
+  if (!(rho > 0.0)) return lbm_fail(h, LBM_ERR_ARG, "rho must be positive");
+  double ux = u ? u[0] : 0.0, uy = u ? u[1] : 0.0, uz = (u && h->lattice == LBM_D3Q19) ? u[2] : 0.0;
+  LBM_CUDA(h, launch_init(h->lattice, h->dtype, h->view(), h->f[h->cur], rho, ux, uy, uz, h->aux_shape()));
+  h->state_ok = true;
+  return LBM_OK;
+}
+
+extern "C" int lbm_set_populations(lbm_handle h, const double *f) {
+  if (!h || !f) return lbm_fail(h, LBM_ERR_ARG, "null argument");
+  if (!h->geom_ok) return lbm_fail(h, LBM_ERR_STATE, "set the geometry first");
+  const size_t bytes = (size_t)h->N * h->Q * sizeof(double);
+  double *d = nullptr;
+  LBM_CUDA(h, cudaMalloc(&d, bytes));
+  cudaError_t e = cudaMemcpyAsync(d, f, bytes, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = launch_set_pop(h->lattice, h->dtype, h->view(), h->f[h->cur], d, h->aux_shape());
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return lbm_fail(h, LBM_ERR_CUDA, cudaGetErrorString(e));
+  h->state_ok = true;
+  return LBM_OK;
+}
+
+extern "C" int lbm_get_populations(lbm_handle h, double *f) {
+  if (!h || !f) return lbm_fail(h, LBM_ERR_ARG, "null argument");
+  if (!h->geom_ok) return lbm_fail(h, LBM_ERR_STATE, "set the geometry first");
+  const size_t bytes = (size_t)h->N * h->Q * sizeof(double);
+  double *d = nullptr;
+  LBM_CUDA(h, cudaMalloc(&d, bytes));
+  cudaError_t e = launch_read(h->lattice, h->dtype, h->view(), h->f[h->cur], d, nullptr, nullptr,
+                              nullptr, h->aux_shape());
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f, d, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return lbm_fail(h, LBM_ERR_CUDA, cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+extern "C" int lbm_macros(lbm_handle h, double *rho, double *u) {
+  if (!h) return lbm_fail(nullptr, LBM_ERR_ARG, "null handle");
+  if (!h->geom_ok || !h->state_ok) return lbm_fail(h, LBM_ERR_STATE, "no state yet");
+  LBM_CUDA(h, launch_read(h->lattice, h->dtype, h->view(), h->f[h->cur], nullptr, rho, u, nullptr,
+                          h->aux_shape()));
+  return LBM_OK;
+}
+
+extern "C" int lbm_mass(lbm_handle h, double *m) {
+  if (!h || !m) return lbm_fail(h, LBM_ERR_ARG, "null argument");
+  if (!h->geom_ok || !h->state_ok) return lbm_fail(h, LBM_ERR_STATE, "no state yet");
+  Launch l = h->aux_shape();
+  const long long nblk = (long long)l.grid.x * l.grid.y * l.grid.z;
+  int rc = h->ensure_scratch(nblk);
+  if (rc) return rc;
+  LBM_CUDA(h, launch_read(h->lattice, h->dtype, h->view(), h->f[h->cur], nullptr, nullptr, nullptr,
+                          h->scratch, l));
+  LBM_CUDA(h, launch_reduce_final(h->scratch, nblk, 1, h->dres, h->stream));
+  LBM_CUDA(h, cudaMemcpyAsync(m, h->dres, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (!std::isfinite(*m)) return lbm_fail(h, LBM_ERR_NONFINITE, "mass is not finite");
+  return LBM_OK;
+}
+
+extern "C" int lbm_wall_force(lbm_handle h, int tag, double F[3]) {
+  if (!h || !F) return lbm_fail(h, LBM_ERR_ARG, "null argument");
+  if (!h->geom_ok || !h->state_ok) return lbm_fail(h, LBM_ERR_STATE, "no state yet");
+  if (tag < -1 || tag > 7) return lbm_fail(h, LBM_ERR_ARG, "tag must be -1..7");
+  F[0] = F[1] = F[2] = 0.0;
+  if (h->nb == 0) return LBM_OK;
+  const int bs = 256;
+  const long long nblk = (h->nb + bs - 1) / bs;
+  int rc = h->ensure_scratch(nblk * 3);
+  if (rc) return rc;
+  Launch l;
+  l.grid = dim3((unsigned)nblk);
+  l.block = dim3(bs);
+  l.stream = h->stream;
+  LBM_CUDA(h, launch_force(h->lattice, h->dtype, h->view(), h->f[h->cur], h->nb, tag, h->scratch, l));
+  LBM_CUDA(h, launch_reduce_final(h->scratch, nblk, 3, h->dres, h->stream));
+  LBM_CUDA(h, cudaMemcpyAsync(F, h->dres, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+extern "C" int lbm_get_counts(lbm_handle h, int64_t *n_fluid, int64_t *n_boundary, int64_t *n_links) {
+  if (!h) return lbm_fail(nullptr, LBM_ERR_ARG, "null handle");
+  if (n_fluid) *n_fluid = h->nfluid;
+  if (n_boundary) *n_boundary = h->nb;
+  if (n_links) *n_links = h->nl;
+  return LBM_OK;
+}
+
+// ---------------------------------------------------------------- stepping
+int lbm_sim::launch_steps(int n) {
+  for (int k = 0; k < n; ++k) {
+    cudaError_t e = launch_step(lattice, dtype, view(), f[cur], f[cur ^ 1], step_shape());
+    if (e != cudaSuccess) return lbm_fail(this, LBM_ERR_CUDA, cudaGetErrorString(e));
+    cur ^= 1;
+  }
+  return LBM_OK;
+}
+
+int lbm_sim::capture(int parity) {
+  // a graph of kGraphSteps (even) steps starting from buffer `parity`
+  const int save = cur;
+  cur = parity;
+  cudaGraph_t g = nullptr;
+  LBM_CUDA(this, cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+  int rc = launch_steps(kGraphSteps);
+  cudaError_t e = cudaStreamEndCapture(stream, &g);
+  cur = save;
+  if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+  if (e != cudaSuccess) return lbm_fail(this, LBM_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&graph[parity], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { graph[parity] = nullptr; return lbm_fail(this, LBM_ERR_CUDA, cudaGetErrorString(e)); }
+  return LBM_OK;
+}
+
+extern "C" int lbm_step(lbm_handle h, int n) {
+  if (!h) return lbm_fail(nullptr, LBM_ERR_ARG, "null handle");
+  if (n < 0) return lbm_fail(h, LBM_ERR_ARG, "negative step count");
+  if (!h->geom_ok || !h->state_ok) return lbm_fail(h, LBM_ERR_STATE, "set geometry and state first");
+  int reps = n / lbm_sim::kGraphSteps;
+  int rest = n % lbm_sim::kGraphSteps;
+  if (reps > 0) {
+    if (!h->graph[h->cur]) {
+      int rc = h->capture(h->cur);
+      if (rc) return rc;
+    }
+    for (int k = 0; k < reps; ++k) LBM_CUDA(h, cudaGraphLaunch(h->graph[h->cur], h->stream));
+  }
+  return h->launch_steps(rest);
+}
+
+// ---------------------------------------------------------------- explicit geometry
+extern "C" int lbm_set_geometry(lbm_handle h, const uint8_t *flags, const double *q, const double *uw,
+                                const double *uw1, const int32_t *tag) {
+  if (!h || !flags) return lbm_fail(h, LBM_ERR_ARG, "null argument");
+  HostGeometry g;
+  std::string msg;
+  int rc = build_records_host(*h, flags, q, uw, uw1, tag, g, msg);
+  if (rc) return lbm_fail(h, rc, msg);
+  return h->upload(g);
+}
+
+int lbm_sim::upload(const HostGeometry &g) {
+  drop_graphs();
+  free_geometry();
+  geom_ok = false;
+  LBM_CUDA(this, cudaMemcpyAsync(flags, g.flags.data(), np, cudaMemcpyHostToDevice, stream));
+  LBM_CUDA(this, cudaMemcpyAsync(cbase, g.cbase.data(), g.cbase.size() * sizeof(uint32_t),
+                                 cudaMemcpyHostToDevice, stream));
+  nb = (long long)g.rec.size();
+  nl = (long long)g.ltag.size();
+  nfluid = g.nfluid;
+  has_uw = g.has_uw;
+  if (nb > 0) {
+    LBM_CUDA(this, cudaMalloc(&rec, nb * sizeof(Rec)));
+    LBM_CUDA(this, cudaMalloc(&rnode, nb * sizeof(uint32_t)));
+    LBM_CUDA(this, cudaMemcpyAsync(rec, g.rec.data(), nb * sizeof(Rec), cudaMemcpyHostToDevice, stream));
+    LBM_CUDA(this, cudaMemcpyAsync(rnode, g.rnode.data(), nb * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
+  }
+  if (nl > 0) {
+    const size_t ls = link_size();
+    LBM_CUDA(this, cudaMalloc(&lq, nl * ls));
+    LBM_CUDA(this, cudaMalloc(&ltag, nl));
+    LBM_CUDA(this, cudaMemcpyAsync(lq, g.lq.data(), nl * ls, cudaMemcpyHostToDevice, stream));
+    LBM_CUDA(this, cudaMemcpyAsync(ltag, g.ltag.data(), nl, cudaMemcpyHostToDevice, stream));
+    if (has_uw) {
+      LBM_CUDA(this, cudaMalloc(&luw, nl * 3 * ls));
+      LBM_CUDA(this, cudaMalloc(&luw1, nl * 3 * ls));
+      LBM_CUDA(this, cudaMemcpyAsync(luw, g.luw.data(), nl * 3 * ls, cudaMemcpyHostToDevice, stream));
+      LBM_CUDA(this, cudaMemcpyAsync(luw1, g.luw1.data(), nl * 3 * ls, cudaMemcpyHostToDevice, stream));
+    }
+  }
+  LBM_CUDA(this, cudaStreamSynchronize(stream));
+  geom_ok = true;
+  return LBM_OK;
+}
+
+extern "C" int lbm_get_geometry(lbm_handle h, uint8_t *flags, double *q, double *uw, double *uw1,
+                                int32_t *tag) {
+  if (!h) return lbm_fail(nullptr, LBM_ERR_ARG, "null handle");
+  if (!h->geom_ok) return lbm_fail(h, LBM_ERR_STATE, "no geometry yet");
+  HostGeometry g;
+  int rc = h->download(g);
+  if (rc) return rc;
+  unpack_geometry(*h, g, flags, q, uw, uw1, tag);
+  return LBM_OK;
+}
+
+int lbm_sim::download(HostGeometry &g) {
+  g.flags.resize(np);
+  g.cbase.resize(np / 32 + 1);
+  g.rec.resize(nb);
+  g.rnode.resize(nb);
+  const size_t ls = link_size();
+  g.lq.resize(nl * ls);
+  g.ltag.resize(nl);
+  g.has_uw = has_uw;
+  g.nfluid = nfluid;
+  LBM_CUDA(this, cudaMemcpyAsync(g.flags.data(), flags, np, cudaMemcpyDeviceToHost, stream));
+  if (nb) {
+    LBM_CUDA(this, cudaMemcpyAsync(g.rec.data(), rec, nb * sizeof(Rec), cudaMemcpyDeviceToHost, stream));
+    LBM_CUDA(this, cudaMemcpyAsync(g.rnode.data(), rnode, nb * sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+  }
+  if (nl) {
+    LBM_CUDA(this, cudaMemcpyAsync(g.lq.data(), lq, nl * ls, cudaMemcpyDeviceToHost, stream));
+    LBM_CUDA(this, cudaMemcpyAsync(g.ltag.data(), ltag, nl, cudaMemcpyDeviceToHost, stream));
+    if (has_uw) {
+      g.luw.resize(nl * 3 * ls);
+      g.luw1.resize(nl * 3 * ls);
+      LBM_CUDA(this, cudaMemcpyAsync(g.luw.data(), luw, nl * 3 * ls, cudaMemcpyDeviceToHost, stream));
+      LBM_CUDA(this, cudaMemcpyAsync(g.luw1.data(), luw1, nl * 3 * ls, cudaMemcpyDeviceToHost, stream));
+    }
+  }
+  LBM_CUDA(this, cudaStreamSynchronize(stream));
+  return LBM_OK;
+}
