@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--dtype", default="f32", choices=list(DTYPE_BYTES))
     ap.add_argument("--bc", default="elibb_f")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--launch", default=None, help="bx,by,variant,tiles of the step kernel (default: autotune)")
+    ap.add_argument("--tune-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -226,6 +229,12 @@ def ours_arm(args, rank, world, dist):
     N = s.N
     np_ = (wl["dims"][0] + 31) // 32 * 32 * wl["dims"][1] * wl["dims"][2]
     stream = s.stream
+    if args.launch:
+        bx, by, var, tiles = (int(t) for t in args.launch.split(","))
+        s.set_launch(bx, by, var, tiles)
+        tuned = {"bx": bx, "by": by, "variant": var, "tiles": tiles, "source": "fixed"}
+    else:
+        tuned = dict(s.autotune(args.tune_steps), source="autotune")
     W_ = max(3, args.warmup)
     s.step(W_)
     s.synchronize()
@@ -258,6 +267,8 @@ def ours_arm(args, rank, world, dist):
     f_host = None
     e2e = None
     try:
+        if args.no_e2e:
+            raise RuntimeError("skipped (--no-e2e)")
         f_host = torch.empty((N, 19), dtype=torch.float64).pin_memory()
         f_host.numpy()[:] = s.get_populations()
         barrier(dist)
@@ -301,7 +312,7 @@ def ours_arm(args, rank, world, dist):
                    "math": "f64" if args.dtype == "f64" else "f32", "nfluid": nfluid, "nodes": N,
                    "boundary_nodes": nb, "wall_links": nl, "l2": "inputs larger than L2 (2 x "
                    f"{19 * np_ * s_bytes / 1e6:.0f} MB population buffers); no flush",
-                   "parallelism": f"replicas x{world}", "graph_steps": 32},
+                   "parallelism": f"replicas x{world}", "graph_steps": 32, "launch": tuned},
         "mlups_all_nodes": round(world * N * args.steps / (ms * 1e-3) / 1e6, 2),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,

@@ -168,6 +168,28 @@ int lbm_get_geometry(lbm_handle h, uint8_t *flags, double *q, double *uw, double
 /* Counts of the current geometry: fluid nodes, boundary nodes, wall links. */
 int lbm_get_counts(lbm_handle h, int64_t *n_fluid, int64_t *n_boundary, int64_t *n_links);
 
+/* Launch configuration of the step kernel:
+ *   bx x by threads per block: bx a multiple of 32 that divides the padded row
+ *     length, bx*by <= 256;
+ *   variant 0..3: the register budget. Variant v guarantees v+1 resident
+ *     256-thread blocks per SM. FP64 storage accepts variant 0 only;
+ *   tiles 1..4: consecutive entries of the step kernel's tile table that one
+ *     block processes. The table lists, plane by plane, the lattice tiles and
+ *     then the boundary-record tiles.
+ * The default is the widest bx <= 128 that divides the row, by = 256/bx,
+ * variant 0, tiles 4. */
+int lbm_set_launch(lbm_handle h, int bx, int by, int variant, int tiles);
+int lbm_get_launch(lbm_handle h, int *bx, int *by, int *variant, int *tiles);
+
+/* Autotuner: runs `steps` steps with each candidate configuration and keeps the
+ * fastest. The candidates are 128- and 256-thread blocks, every admissible bx,
+ * every register variant, and 1, 2 or 4 tiles per block. Each is timed with
+ * CUDA events. The simulation advances by every trial step. Writes the chosen
+ * configuration and its time per step in ms; any output may be NULL.
+ * Synchronises the stream. */
+int lbm_autotune(lbm_handle h, int steps, int *bx, int *by, int *variant, int *tiles,
+                 double *ms_per_step);
+
 /* Wait for all work on the handle's stream. */
 int lbm_synchronize(lbm_handle h);
 

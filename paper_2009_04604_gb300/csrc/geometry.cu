@@ -19,7 +19,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/lbm.h"
+#include "lbm.h"
 #include "geometry.hpp"
 #include "sim.hpp"
 
@@ -242,8 +242,8 @@ __global__ void k_geo_fill(const GeoView g, const uint32_t *__restrict__ cbase,
   const uint32_t lt = (1u << (threadIdx.x & 31)) - 1u;
   const uint32_t rid = cbase[n >> 5] + __popc(bal & lt);
   r.link0 = lbase[n >> 5] + s - cnt;
-  rec[rid] = r;
   rnode[rid] = (uint32_t)n;
+  bool moving_node = false;
   const double X[3] = {(double)x, (double)y, (double)z};
   const int cell = cell_of(g, x, y, z);
   uint32_t li = r.link0;
@@ -292,11 +292,15 @@ __global__ void k_geo_fill(const GeoView g, const uint32_t *__restrict__ cbase,
         tg = sh.tag;
       }
     }
+    if (u0[0] != 0.0 || u0[1] != 0.0 || u0[2] != 0.0 || u1[0] != 0.0 || u1[1] != 0.0 || u1[2] != 0.0)
+      moving_node = true;
     lq[li] = (LT)qq;
     ltag[li] = (uint8_t)tg;
     if (luw) for (int a = 0; a < 3; ++a) { luw[3 * li + a] = (LT)u0[a]; luw1[3 * li + a] = (LT)u1[a]; }
     ++li;
   }
+  if (moving_node) r.open |= REC_MOVING;
+  rec[rid] = r;
 }
 
 }  // namespace lbm
@@ -404,6 +408,7 @@ extern "C" int lbm_build_geometry(lbm_handle h, const uint8_t *base, const doubl
   cudaStream_t st = h->stream;
   h->drop_graphs();
   h->free_geometry();
+  h->tiles_bx = h->tiles_by = 0;
   h->geom_ok = false;
   if (base) {
     GEO_CUDA(cudaMalloc(&d_base, h->N));

@@ -6,7 +6,7 @@
 #include <cmath>
 #include <cstring>
 
-#include "../../include/lbm.h"
+#include "lbm.h"
 #include "geometry.hpp"
 #include "sim.hpp"
 
@@ -93,6 +93,13 @@ int build_records_host(const lbm_sim &s, const uint8_t *flags, const double *q, 
         continue;
       }
       r.link0 = (uint32_t)(g.ltag.size());
+      if (moving)
+        for (int i = 0; i < Q; ++i) {
+          if (!(r.cut & (1u << i))) continue;
+          const long long li = hn * Q + i;
+          for (int a = 0; a < 3; ++a)
+            if ((uw && uw[li * 3 + a] != 0.0) || (uw1 && uw1[li * 3 + a] != 0.0)) r.open |= REC_MOVING;
+        }
       g.rec.push_back(r);
       g.rnode.push_back((uint32_t)n);
       g.flags[n] |= F_BOUNDARY;

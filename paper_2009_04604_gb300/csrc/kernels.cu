@@ -50,12 +50,31 @@ static cudaError_t dispatch(int lattice, int dtype, Fn &&fn) {
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_step(int lattice, int dtype, const View &v, const void *fin, void *fout,
-                        const Launch &l) {
+// The step grid is 1-D, one block per entry of the tile table (l.grid.x entries).
+template <class L, typename S, typename M, int MINB>
+static cudaError_t step_variant(const View &v, const void *fin, void *fout, const Launch &l) {
+  if (v.has_force)
+    k_step<L, S, M, MINB, true><<<l.grid, l.block, 0, l.stream>>>(v, static_cast<const S *>(fin),
+                                                                  static_cast<S *>(fout));
+  else
+    k_step<L, S, M, MINB, false><<<l.grid, l.block, 0, l.stream>>>(v, static_cast<const S *>(fin),
+                                                                   static_cast<S *>(fout));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step(int lattice, int dtype, int variant, const View &v, const void *fin,
+                        void *fout, const Launch &l) {
   return dispatch(lattice, dtype, [&]<class L, typename S, typename M>() {
-    k_step<L, S, M><<<l.grid, l.block, 0, l.stream>>>(v, static_cast<const S *>(fin),
-                                                      static_cast<S *>(fout));
-    return cudaGetLastError();
+    if constexpr (sizeof(M) == 8) {
+      return step_variant<L, S, M, 1>(v, fin, fout, l);  // FP64: one register budget
+    } else {
+      switch (variant) {
+        case 1: return step_variant<L, S, M, 2>(v, fin, fout, l);
+        case 2: return step_variant<L, S, M, 3>(v, fin, fout, l);
+        case 3: return step_variant<L, S, M, 4>(v, fin, fout, l);
+        default: return step_variant<L, S, M, 1>(v, fin, fout, l);
+      }
+    }
   });
 }
 

@@ -55,6 +55,22 @@ __device__ __forceinline__ void bfl_complete(const View &v, const Rec &r, M (&f)
   }
 }
 
+// Inverse of bfl_complete: the slot of a BFL link with q < 1/2 holds the value minus
+// (1-2q) f*_ibar(x_FF), so that the gather's completion restores it. Used when a
+// state is written from outside (initialisation, set_populations).
+template <class L, typename M>
+__device__ __forceinline__ void bfl_encode(const View &v, const Rec &r, M (&f)[L::Q]) {
+  const M *lq = static_cast<const M *>(v.lq);
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    const uint32_t bit = 1u << i;
+    if (r.cut & r.ffok & bit) {
+      const M q = lq[r.link0 + __popc(r.cut & (bit - 1u))];
+      if (q < M(0.5)) f[i] -= (M(1) - M(2) * q) * f[opp<L>(i)];
+    }
+  }
+}
+
 // Record of a boundary node. bal is the warp ballot of the boundary flag, taken by
 // a warp that covers 32 consecutive nodes of one row (one 32-node chunk).
 __device__ __forceinline__ const Rec *record_of(const View &v, long long n, uint32_t bal) {
@@ -68,24 +84,30 @@ struct Macro {
   M drho, rho, ux, uy, uz, usq;
 };
 
+// Density deviation and Guo-corrected velocity, summed over opposite pairs
+// (f_i + f_ibar and f_i - f_ibar), with the rest population in the middle slot.
 template <class L, typename M>
 __device__ __forceinline__ Macro<L, M> moments(const View &v, const M (&f)[L::Q]) {
-  M d = M(0), jx = M(0), jy = M(0), jz = M(0);
+  constexpr int R = L::Q / 2;
+  M d = f[R], jx = M(0), jy = M(0), jz = M(0);
 #pragma unroll
-  for (int i = 0; i < L::Q; ++i) {
-    d += f[i];
-    if (L::cx(i) > 0) jx += f[i]; else if (L::cx(i) < 0) jx -= f[i];
-    if (L::cy(i) > 0) jy += f[i]; else if (L::cy(i) < 0) jy -= f[i];
-    if (L::cz(i) > 0) jz += f[i]; else if (L::cz(i) < 0) jz -= f[i];
+  for (int i = 0; i < R; ++i) {
+    const int j = L::Q - 1 - i;
+    const M sum = f[i] + f[j], dif = f[i] - f[j];
+    d += sum;
+    if (L::cx(i) > 0) jx += dif; else if (L::cx(i) < 0) jx -= dif;
+    if (L::cy(i) > 0) jy += dif; else if (L::cy(i) < 0) jy -= dif;
+    if (L::cz(i) > 0) jz += dif; else if (L::cz(i) < 0) jz -= dif;
   }
+  const Par<M> P(v);
   Macro<L, M> m;
   m.drho = d;
-  m.rho = M(v.rho0) + d;
+  m.rho = P.rho0 + d;
   const M inv = M(1) / m.rho;
   if (v.has_force) {  // Guo: u = (sum c f + F/2) / rho
-    jx += M(0.5 * v.F[0]);
-    jy += M(0.5 * v.F[1]);
-    jz += M(0.5 * v.F[2]);
+    jx += M(0.5) * P.F[0];
+    jy += M(0.5) * P.F[1];
+    jz += M(0.5) * P.F[2];
   }
   m.ux = jx * inv;
   m.uy = jy * inv;
@@ -104,19 +126,62 @@ __device__ __forceinline__ M feq_s(int i, M drho, M rho, M ux, M uy, M uz, M usq
 // Guo source (1 - omega/2) w_i [3 (c_i - u).F + 9 (c_i.u)(c_i.F)]
 template <class L, typename M>
 __device__ __forceinline__ M guo(const View &v, int i, const Macro<L, M> &m) {
-  const M Fx = M(v.F[0]), Fy = M(v.F[1]), Fz = M(v.F[2]);
+  const Par<M> P(v);
+  const M Fx = P.F[0], Fy = P.F[1], Fz = P.F[2];
   const M cu = M(L::cx(i)) * m.ux + M(L::cy(i)) * m.uy + M(L::cz(i)) * m.uz;
   const M cF = M(L::cx(i)) * Fx + M(L::cy(i)) * Fy + M(L::cz(i)) * Fz;
   const M uF = m.ux * Fx + m.uy * Fy + m.uz * Fz;
-  return (M(1) - M(0.5 * v.omega)) * M(weight<L>(i)) * (M(3) * (cF - uF) + M(9) * cu * cF);
+  return (M(1) - M(0.5) * P.omega) * M(weight<L>(i)) * (M(3) * (cF - uF) + M(9) * cu * cF);
 }
 
 // post-collision shifted population f*_i = f_i + omega (f^eq_i - f_i) + S_i
 template <class L, typename M>
 __device__ __forceinline__ M post(const View &v, int i, const M fi, const Macro<L, M> &m) {
-  M r = fi + M(v.omega) * (feq_s<L, M>(i, m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - fi);
+  M r = fi + Par<M>(v).omega * (feq_s<L, M>(i, m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - fi);
   if (v.has_force) r += guo<L, M>(v, i, m);
   return r;
+}
+
+// Bulk BGK relaxation and store, by opposite pairs (i, ibar). With
+// omega f^eq_i = w [omega (drho - 3/2 rho u^2) + 9/2 omega rho (c.u)^2] + 3 w omega rho (c.u),
+// the even part is shared by the pair and the odd part flips sign, and
+// f*_i = (1 - omega) f_i + omega f^eq_i + S_i. The Guo source splits the same way:
+// S = k w (9 (c.u)(c.F) - 3 u.F) + 3 k w (c.F), with k = 1 - omega/2.
+template <class L, typename S, typename M, bool FORCE>
+__device__ __forceinline__ void collide_store(const View &v, const M (&f)[L::Q], const Macro<L, M> &m,
+                                              S *__restrict__ dst, int np) {
+  constexpr int R = L::Q / 2;
+  const Par<M> P(v);
+  const M om = P.omega, omr = M(1) - om;
+  const M wr = om * m.rho;
+  const M b0 = om * (m.drho - M(1.5) * m.rho * m.usq);
+  M Fx = M(0), Fy = M(0), Fz = M(0), kf = M(0), uF = M(0);
+  if constexpr (FORCE) {
+    Fx = P.F[0]; Fy = P.F[1]; Fz = P.F[2];
+    kf = M(1) - M(0.5) * om;
+    uF = m.ux * Fx + m.uy * Fy + m.uz * Fz;
+  }
+  {
+    const M w = M(weight<L>(R));
+    M eq = w * b0;
+    if constexpr (FORCE) eq -= M(3) * kf * w * uF;
+    dst[R * np] = to_store<S, M>(omr * f[R] + eq);
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int j = L::Q - 1 - i;
+    const M w = M(weight<L>(i));
+    const M cu = M(L::cx(i)) * m.ux + M(L::cy(i)) * m.uy + M(L::cz(i)) * m.uz;
+    M sym = w * (b0 + M(4.5) * wr * cu * cu);
+    M asym = M(3) * w * wr * cu;
+    if constexpr (FORCE) {
+      const M cF = M(L::cx(i)) * Fx + M(L::cy(i)) * Fy + M(L::cz(i)) * Fz;
+      sym += kf * w * (M(9) * cu * cF - M(3) * uF);
+      asym += M(3) * kf * w * cF;
+    }
+    dst[i * np] = to_store<S, M>(omr * f[i] + (sym + asym));
+    dst[j * np] = to_store<S, M>(omr * f[j] + (sym - asym));
+  }
 }
 
 // ---------------------------------------------------------------- boundary rule
@@ -126,58 +191,102 @@ __device__ __forceinline__ M post(const View &v, int i, const M fi, const Macro<
 //   g  = f*_ibar(x_F) + ME, ME = 2 w_i rho_F c_i.u_w / c_s^2 (Eq. ME-solid-to-fluid)  s = 1-q
 //   f1 = f~*_i(x_W) = f^eq_i(rho_F, u_w(t)) + (1 - omega) f^neq_ibar(x_F)          s = 1
 //   h  = f*_i(x_F)                                                                 s = 1+q
-// Weights: Lagrange weights (Eq. poli_coeff) at s_ref = q, in closed form.
+// Weights: Lagrange weights (Eq. poli_coeff) at s_ref = q, in closed form. At
+// q = 1/2 every rule reduces exactly to g (half-way bounce-back).
+// The loop runs over the set bits of the link masks with a run-time direction
+// index, which keeps the code small. The node's populations sit in shared memory
+// (fs[i*stride]), and the direction constants come from packed words.
+
+// shifted equilibrium for a run-time direction
+template <class L, typename M>
+__device__ __forceinline__ M feq_r(int i, M drho, M rho, M ux, M uy, M uz, M usq) {
+  const M cu = M(dcx<L>(i)) * ux + M(dcy<L>(i)) * uy + M(dcz<L>(i)) * uz;
+  return dweight<L, M>(i) * (drho + rho * (M(3) * cu + M(4.5) * cu * cu - M(1.5) * usq));
+}
+
+// post-collision (with Guo source) for a run-time direction
+template <class L, typename M>
+__device__ __forceinline__ M post_r(const View &v, const Par<M> &P, int i, M fi, const Macro<L, M> &m) {
+  M r = fi + P.omega * (feq_r<L, M>(i, m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - fi);
+  if (v.has_force) {
+    const M cx = M(dcx<L>(i)), cy = M(dcy<L>(i)), cz = M(dcz<L>(i));
+    const M cu = cx * m.ux + cy * m.uy + cz * m.uz;
+    const M cF = cx * P.F[0] + cy * P.F[1] + cz * P.F[2];
+    const M uF = m.ux * P.F[0] + m.uy * P.F[1] + m.uz * P.F[2];
+    r += (M(1) - M(0.5) * P.omega) * dweight<L, M>(i) * (M(3) * (cF - uF) + M(9) * cu * cF);
+  }
+  return r;
+}
+
+// element offset of node (x, y, z) - c, with the periodic and sheared wraps
+__device__ __forceinline__ int upstream_offset(const View &v, int x, int y, int z, int cx, int cy, int cz) {
+  int X = x - cx, Y = y - cy, Z = z - cz;
+  if (X < 0) { X += v.nx; Y += v.xshift; }
+  else if (X >= v.nx) { X -= v.nx; Y -= v.xshift; }
+  if (v.xshift != 0) { Y %= v.ny; if (Y < 0) Y += v.ny; }
+  else { Y = Y < 0 ? Y + v.ny : (Y >= v.ny ? Y - v.ny : Y); }
+  Z = Z < 0 ? Z + v.nz : (Z >= v.nz ? Z - v.nz : Z);
+  return ((Z - z) * v.ny + (Y - y)) * v.nxp + (X - x);
+}
+
 template <class L, typename S, typename M>
-__device__ __forceinline__ void boundary(const View &v, const Rec &r, const M (&f)[L::Q],
-                                         const Macro<L, M> &m, long long n, const Nbr &nb,
-                                         S *__restrict__ fout) {
+__device__ void boundary(const View &v, const Rec &r, const M *fs, int stride, const Macro<L, M> &m,
+                         long long n, int x, int y, int z, S *__restrict__ fout) {
   const M *lq = static_cast<const M *>(v.lq);
   const M *luw = static_cast<const M *>(v.luw);
   const M *luw1 = static_cast<const M *>(v.luw1);
-  const M om = M(v.omega);
-#pragma unroll
-  for (int i = 0; i < L::Q; ++i) {
+  const Par<M> P(v);
+  const uint32_t open = r.open & ~REC_MOVING;
+  const bool moving = v.has_uw && (r.open & REC_MOVING);
+  uint32_t links = r.cut | open;
+#pragma unroll 1
+  while (links) {
+    const int i = __ffs(links) - 1;
     const uint32_t bit = 1u << i;
-    if (!((r.cut | r.open) & bit)) continue;
+    links &= links - 1u;
     const int ib = opp<L>(i);
-    const M fneq_ib = f[ib] - feq_s<L, M>(ib, m.drho, m.rho, m.ux, m.uy, m.uz, m.usq);
+    const int cx = dcx<L>(i), cy = dcy<L>(i), cz = dcz<L>(i);
+    const M fib = fs[ib * stride];
     M val;
-    if (r.open & bit) {
+    if (open & bit) {
       // single-node pressure outlet: f^eq_i(rho0, u_F) + f^neq_ibar(x_F)
-      val = feq_s<L, M>(i, M(0), M(v.rho0), m.ux, m.uy, m.uz, m.usq) + fneq_ib;
+      const M fneq_ib = fib - feq_r<L, M>(ib, m.drho, m.rho, m.ux, m.uy, m.uz, m.usq);
+      val = feq_r<L, M>(i, M(0), P.rho0, m.ux, m.uy, m.uz, m.usq) + fneq_ib;
     } else {
       const uint32_t li = r.link0 + __popc(r.cut & (bit - 1u));
       const M q = lq[li];
       M wx = M(0), wy = M(0), wz = M(0), vx = M(0), vy = M(0), vz = M(0);
-      if (v.has_uw) {
+      if (moving) {
         wx = luw[3 * li]; wy = luw[3 * li + 1]; wz = luw[3 * li + 2];
         vx = luw1[3 * li]; vy = luw1[3 * li + 1]; vz = luw1[3 * li + 2];
       }
-      const M cu0 = M(L::cx(i)) * wx + M(L::cy(i)) * wy + M(L::cz(i)) * wz;
-      const M me = M(6.0 * weight<L>(i)) * m.rho * cu0;
-      const M g = post<L, M>(v, ib, f[ib], m) + me;
-      if (v.bc == BC_HWBB) {
+      const M w = dweight<L, M>(i);
+      const M cu0 = M(cx) * wx + M(cy) * wy + M(cz) * wz;
+      const M me = M(6) * w * m.rho * cu0;
+      const M g = post_r<L, M>(v, P, ib, fib, m) + me;
+      if (v.bc == BC_HWBB || q == M(0.5)) {
         val = g;
       } else if (v.bc == BC_BFL) {
         if (q < M(0.5)) {
           val = (r.ffok & bit) ? M(2) * q * g + (M(1) - M(2) * q) * me : g;
         } else {
-          const M h = post<L, M>(v, i, f[i], m);
+          const M h = post_r<L, M>(v, P, i, fs[i * stride], m);
           val = (g + (M(2) * q - M(1)) * h) / (M(2) * q);
         }
       } else {
+        const M fneq_ib = fib - feq_r<L, M>(ib, m.drho, m.rho, m.ux, m.uy, m.uz, m.usq);
         const M u0sq = wx * wx + wy * wy + wz * wz;
-        const M u1sq = vx * vx + vy * vy + vz * vz;
-        const M f1 = feq_s<L, M>(i, m.drho, m.rho, wx, wy, wz, u0sq) + (M(1) - om) * fneq_ib;
+        const M f1 = feq_r<L, M>(i, m.drho, m.rho, wx, wy, wz, u0sq) + (M(1) - P.omega) * fneq_ib;
         if (q < M(0.5)) {
-          const M f0 = feq_s<L, M>(i, m.drho, m.rho, vx, vy, vz, u1sq) + fneq_ib;
-          if (v.bc == BC_ELIBB_FQ && q >= M(v.qcut))
+          const M u1sq = vx * vx + vy * vy + vz * vz;
+          const M f0 = feq_r<L, M>(i, m.drho, m.rho, vx, vy, vz, u1sq) + fneq_ib;
+          if (v.bc == BC_ELIBB_FQ && q >= P.qcut)
             val = (M(1) - M(2) * q) * f0 + g + (M(2) * q - M(1)) * f1;
           else
             val = ((M(1) - M(2) * q) * f0 + q * g) / (M(1) - q);
         } else {
           if (v.bc == BC_ELIBB_FQ) {
-            const M h = post<L, M>(v, i, f[i], m);
+            const M h = post_r<L, M>(v, P, i, fs[i * stride], m);
             const M a = M(2) * q - M(1);
             val = ((M(1) - q) * g + M(2) * a * f1 + a * (q - M(1)) * h) / (M(2) * q * q);
           } else {
@@ -186,39 +295,119 @@ __device__ __forceinline__ void boundary(const View &v, const Rec &r, const M (&
         }
       }
     }
-    fout[(long long)i * v.np + n + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))] = to_store<S, M>(val);
+    fout[(long long)i * v.np + n + upstream_offset(v, x, y, z, cx, cy, cz)] = to_store<S, M>(val);
   }
 }
 
-// ---------------------------------------------------------------- the fused step
-// One thread per node. blockDim.x is a multiple of 32 and divides nxp, so every
-// warp covers one aligned 32-node chunk of one row.
+// The boundary work of one boundary node: the node's own pre-collision
+// populations (gathered from fin, which is unchanged during the step, and
+// BFL-completed), its moments, and the written-ahead unknowns of its wall and
+// open links. fs is this thread's column of the block's shared staging array.
 template <class L, typename S, typename M>
-__global__ void __launch_bounds__(256) k_step(const View v, const S *__restrict__ fin,
-                                              S *__restrict__ fout) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  if (y >= v.ny) return;  // uniform across the warp
-  const long long n = ((long long)z * v.ny + y) * v.nxp + x;
-  const uint8_t fl = v.flags[n];
-  const uint32_t bal = __ballot_sync(0xffffffffu, fl & F_BOUNDARY);
-  if ((fl & 3) != K_FLUID) return;
+__device__ __forceinline__ void boundary_node(const View &v, const Rec r, const S *__restrict__ fin,
+                                              S *__restrict__ fout, long long n, int x, int y, int z,
+                                              M *fs, int stride) {
   Nbr nb;
   nb.init(v, x, y, z);
   M f[L::Q];
   gather<L, S, M>(v, fin, n, nb, f);
-  const bool isb = fl & F_BOUNDARY;
-  Rec r = {0u, 0u, 0u, 0u};
-  if (isb) {
-    r = *record_of(v, n, bal);
-    if (v.bc == BC_BFL) bfl_complete<L, M>(v, r, f);
-  }
+  if (v.bc == BC_BFL) bfl_complete<L, M>(v, r, f);
   const Macro<L, M> m = moments<L, M>(v, f);
 #pragma unroll
-  for (int i = 0; i < L::Q; ++i)
-    fout[(long long)i * v.np + n] = to_store<S, M>(post<L, M>(v, i, f[i], m));
-  if (isb) boundary<L, S, M>(v, r, f, m, n, nb, fout);
+  for (int i = 0; i < L::Q; ++i) fs[i * stride] = f[i];
+  boundary<L, S, M>(v, r, fs, stride, m, n, x, y, z, fout);
+}
+
+// ---------------------------------------------------------------- the fused step
+// One launch does the whole update t -> t+1. Each block takes one entry of the
+// tile table v.tiles:
+//  - lattice tile {z, t}: a bx-by-by block of plane z (bx a multiple of 32 that
+//    divides nxp, so a warp covers one 32-node chunk of a row). Every fluid
+//    node, boundary nodes included, is gathered, relaxed and stored;
+//  - boundary tile {-1 - count, first}: records first .. first+count-1, one
+//    thread per boundary node. Each evaluates the boundary rule of its node
+//    and writes the unknowns ahead into the non-fluid slots that only this
+//    node reads.
+// The table lists plane z's boundary tiles right after its lattice tiles. The
+// boundary threads' gathers then hit the lines the plane's lattice threads have
+// just brought into L2, and their written-ahead values complete the same
+// sectors in L2. The two kinds touch disjoint output slots and only read fin,
+// so they need no ordering. Dense boundary tiles keep the rule off the lattice
+// warps, where wall rows would otherwise diverge into it for every lane.
+// MINB is the minimum number of resident 256-thread blocks per SM that the
+// register allocation must allow (1: unconstrained); the autotuner picks it.
+// FORCE selects the body-force path at compile time. Element offsets are 32-bit,
+// since the library keeps Q x padded nodes below 2^31 per simulation.
+// Lattice tile {z, t} of the table: gather, relax and store every fluid node.
+template <class L, typename S, typename M, bool FORCE>
+__device__ __forceinline__ void lattice_tile(const View &v, const S *__restrict__ fin,
+                                             S *__restrict__ fout, int2 tile) {
+  const int x = (tile.y % v.gx) * blockDim.x + threadIdx.x;
+  const int y = (tile.y / v.gx) * blockDim.y + threadIdx.y;
+  const int z = tile.x;
+  if (y >= v.ny) return;  // uniform across the warp
+  const int n = (z * v.ny + y) * v.nxp + x;
+  const uint8_t fl = v.flags[n];
+  uint32_t bal = 0;
+  if (v.bc == BC_BFL) bal = __ballot_sync(0xffffffffu, fl & F_BOUNDARY);
+  if ((fl & 3) != K_FLUID) return;
+  const int np = (int)v.np;
+  M f[L::Q];
+  const bool interior = x > 0 && x < v.nx - 1 && y > 0 && y < v.ny - 1 &&
+                        (L::D == 2 || (z > 0 && z < v.nz - 1));
+  if (interior) {
+    // no wrap: the source of population i is n - c_i, at an offset that is the same
+    // for every thread, so each load is a per-thread base plus a uniform offset
+    const int plane = v.nxp * v.ny;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      const S *__restrict__ p = fin + (i * np - (L::cx(i) + L::cy(i) * v.nxp + L::cz(i) * plane));
+      f[i] = to_math<S, M>(__ldg(p + n));
+    }
+  } else {
+    Nbr nb;
+    nb.init(v, x, y, z);
+    const S *__restrict__ src = fin + n;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+      f[i] = to_math<S, M>(__ldg(src + (i * np + nb.at(-L::cx(i), -L::cy(i), -L::cz(i)))));
+  }
+  if (v.bc == BC_BFL && (fl & F_BOUNDARY)) bfl_complete<L, M>(v, *record_of(v, n, bal), f);
+  const Macro<L, M> m = moments<L, M>(v, f);
+  collide_store<L, S, M, FORCE>(v, f, m, fout + n, np);
+}
+
+// Boundary tile {-1 - count, first}: one thread per boundary record.
+template <class L, typename S, typename M>
+__device__ __forceinline__ void boundary_tile(const View &v, const S *__restrict__ fin,
+                                              S *__restrict__ fout, int2 tile, M *stage) {
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  if (t >= -1 - tile.x) return;
+  const int rid = tile.y + t;
+  const Rec r = v.rec[rid];
+  const int n = (int)v.rnode[rid];
+  const int x = n % v.nxp, y = (n / v.nxp) % v.ny, z = n / (v.nxp * v.ny);
+  boundary_node<L, S, M>(v, r, fin, fout, n, x, y, z, stage + t, 256);
+}
+
+// Block b takes table entries b*T .. b*T+T-1 (T = v.tpb_tiles <= 4), whose
+// descriptors it loads together up front.
+template <class L, typename S, typename M, int MINB, bool FORCE>
+__global__ void __launch_bounds__(256, MINB) k_step(const View v, const S *__restrict__ fin,
+                                                    S *__restrict__ fout) {
+  __shared__ M stage[L::Q * 256];  // boundary tiles: populations, [direction][thread]
+  const int T = v.tpb_tiles;
+  const int first = blockIdx.x * T;
+  int2 tl[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (k < T && first + k < v.ntiles) tl[k] = v.tiles[first + k];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (k >= T || first + k >= v.ntiles) break;
+    if (tl[k].x < 0) boundary_tile<L, S, M>(v, fin, fout, tl[k], stage);
+    else lattice_tile<L, S, M, FORCE>(v, fin, fout, tl[k]);
+  }
 }
 
 // ---------------------------------------------------------------- state set-up and read-out
@@ -231,14 +420,19 @@ __global__ void k_init(const View v, S *__restrict__ fout, double rho, double ux
   const int z = blockIdx.z;
   if (y >= v.ny) return;
   const long long n = ((long long)z * v.ny + y) * v.nxp + x;
-  if ((v.flags[n] & 3) != K_FLUID) return;
+  const uint8_t fl = v.flags[n];
+  const uint32_t bal = __ballot_sync(0xffffffffu, fl & F_BOUNDARY);
+  if ((fl & 3) != K_FLUID) return;
   Nbr nb;
   nb.init(v, x, y, z);
   const M usq = M(ux * ux + uy * uy + uz * uz);
+  M f[L::Q];
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) f[i] = feq_s<L, M>(i, M(rho - v.rho0), M(rho), M(ux), M(uy), M(uz), usq);
+  if ((fl & F_BOUNDARY) && v.bc == BC_BFL) bfl_encode<L, M>(v, *record_of(v, n, bal), f);
 #pragma unroll
   for (int i = 0; i < L::Q; ++i)
-    fout[(long long)i * v.np + n + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))] = to_store<S, M>(
-        feq_s<L, M>(i, M(rho - v.rho0), M(rho), M(ux), M(uy), M(uz), usq));
+    fout[(long long)i * v.np + n + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))] = to_store<S, M>(f[i]);
 }
 
 // Host-layout FP64 populations fh[(x + nx*(y + ny*z))*Q + i] -> slots (unshifted in, shifted stored).
@@ -247,16 +441,21 @@ __global__ void k_set_pop(const View v, S *__restrict__ fout, const double *__re
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
-  if (y >= v.ny || x >= v.nx) return;
+  if (y >= v.ny) return;
   const long long n = ((long long)z * v.ny + y) * v.nxp + x;
-  if ((v.flags[n] & 3) != K_FLUID) return;
+  const uint8_t fl = v.flags[n];
+  const uint32_t bal = __ballot_sync(0xffffffffu, fl & F_BOUNDARY);
+  if ((fl & 3) != K_FLUID) return;  // also every padding node (x >= nx)
   const long long hn = ((long long)z * v.ny + y) * v.nx + x;
   Nbr nb;
   nb.init(v, x, y, z);
+  M f[L::Q];
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) f[i] = M(fh[hn * L::Q + i] - weight<L>(i) * v.rho0);
+  if ((fl & F_BOUNDARY) && v.bc == BC_BFL) bfl_encode<L, M>(v, *record_of(v, n, bal), f);
 #pragma unroll
   for (int i = 0; i < L::Q; ++i)
-    fout[(long long)i * v.np + n + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))] =
-        to_store<S, M>(M(fh[hn * L::Q + i] - weight<L>(i) * v.rho0));
+    fout[(long long)i * v.np + n + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))] = to_store<S, M>(f[i]);
 }
 
 // Pre-collision populations (gathered, BFL-completed), macroscopic fields, and the

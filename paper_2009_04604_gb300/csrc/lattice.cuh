@@ -54,6 +54,34 @@ __host__ __device__ constexpr double weight(int i) {
 template <class L>
 __host__ __device__ constexpr int opp(int i) { return L::Q - 1 - i; }
 
+// Run-time direction index: the velocity components packed as 2-bit fields
+// (component + 1) in 64-bit constants, and the weight in the math type. These
+// keep a rolled loop over links free of lookup chains and of FP64 arithmetic.
+template <class L>
+__host__ __device__ constexpr unsigned long long pack_c(int comp) {
+  unsigned long long p = 0;
+  for (int i = 0; i < L::Q; ++i) {
+    const int c = comp == 0 ? L::cx(i) : (comp == 1 ? L::cy(i) : L::cz(i));
+    p |= (unsigned long long)(c + 1) << (2 * i);
+  }
+  return p;
+}
+template <class L>
+__device__ __forceinline__ int dcx(int i) { return (int)((pack_c<L>(0) >> (2 * i)) & 3ull) - 1; }
+template <class L>
+__device__ __forceinline__ int dcy(int i) { return (int)((pack_c<L>(1) >> (2 * i)) & 3ull) - 1; }
+template <class L>
+__device__ __forceinline__ int dcz(int i) { return (int)((pack_c<L>(2) >> (2 * i)) & 3ull) - 1; }
+template <class L, typename M>
+__device__ __forceinline__ M dweight(int i) {
+  const int a = dcx<L>(i), b = dcy<L>(i), c = dcz<L>(i);
+  const int k = a * a + b * b + c * c;
+  constexpr M w0 = M(weight<L>(L::Q / 2));  // rest
+  constexpr M w1 = M(L::Q == 9 ? 1.0 / 9.0 : 1.0 / 18.0);
+  constexpr M w2 = M(1.0 / 36.0);
+  return k == 0 ? w0 : (k == 1 ? w1 : w2);
+}
+
 // ---- storage <-> math conversions (round to nearest even on store) ----
 template <typename S, typename M> __device__ __forceinline__ M to_math(S v);
 template <> __device__ __forceinline__ double to_math<double, double>(double v) { return v; }
@@ -76,9 +104,10 @@ template <> __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16, flo
 enum : uint8_t { K_FLUID = 0, K_SOLID = 1, K_OPEN = 2, K_PAD = 3, F_BOUNDARY = 4 };
 
 // Boundary record of one boundary node (records are sorted by node index).
+constexpr uint32_t REC_MOVING = 1u << 31;  // in Rec::open: the node has moving wall links
 struct Rec {
   uint32_t cut;   // bit i: link i is a wall link (node n - c_i is SOLID)
-  uint32_t open;  // bit i: link i is an open link (node n - c_i is OPEN)
+  uint32_t open;  // bit i: link i is an open link (node n - c_i is OPEN); bit 31: REC_MOVING
   uint32_t ffok;  // bit i: the second node along the link, n + c_i, is fluid (BFL)
   uint32_t link0; // index of the first wall link of this node in the link arrays
 };
@@ -92,13 +121,33 @@ struct View {
   double omega, rho0, qcut;  // 1/tau, reference density, ELIBB-FQ cutoff
   double F[3];               // body-force density
   int has_force, has_uw;
+  // the same scalars in FP32, so that FP32 kernels convert nothing on the
+  // (slow) FP64 pipe: omega, rho0, qcut, F
+  float omega_f, rho0_f, qcut_f, F_f[3];
   const uint8_t *flags;      // [np]
   const uint32_t *cbase;     // [np/32] records before each 32-node chunk
   const Rec *rec;            // [nb]
   const uint32_t *rnode;     // [nb] padded node index of each record
+  long long nb;              // number of boundary records
+  const int2 *tiles;         // step-kernel block table (see k_step)
+  int gx;                    // lattice tiles per row of tiles (nxp / block x)
+  int ntiles, tpb_tiles;     // table length; consecutive table entries per block
   const void *lq;            // [nl] q of each wall link (math type)
   const void *luw, *luw1;    // [nl*3] wall velocity at t, t+1 (math type) or null
   const uint8_t *ltag;       // [nl] force tag of each wall link
+};
+
+// Scalar parameters in the math type of a kernel.
+template <typename M> struct Par;
+template <> struct Par<double> {
+  double omega, rho0, qcut, F[3];
+  __device__ __forceinline__ explicit Par(const View &v)
+      : omega(v.omega), rho0(v.rho0), qcut(v.qcut), F{v.F[0], v.F[1], v.F[2]} {}
+};
+template <> struct Par<float> {
+  float omega, rho0, qcut, F[3];
+  __device__ __forceinline__ explicit Par(const View &v)
+      : omega(v.omega_f), rho0(v.rho0_f), qcut(v.qcut_f), F{v.F_f[0], v.F_f[1], v.F_f[2]} {}
 };
 
 // Relative element offsets of the 27 neighbours (dx, dy, dz in {-1,0,1}) of a node,
@@ -106,7 +155,7 @@ struct View {
 // dx = a-1, dy = b-1; oz[c] covers z for dz = c-1.
 struct Nbr {
   int oxy[3][3];
-  long long oz[3];
+  int oz[3];  // 32-bit: a simulation keeps Q x padded nodes below 2^31
 
   __device__ __forceinline__ void init(const View &v, int x, int y, int z) {
     const int xs[3] = {x == 0 ? v.nx - 1 : x - 1, x, x == v.nx - 1 ? 0 : x + 1};
@@ -127,15 +176,15 @@ struct Nbr {
         oxy[a][b] = (yy - y) * v.nxp + (xs[a] - x);
       }
     }
-    const long long plane = (long long)v.nxp * v.ny;
+    const int plane = v.nxp * v.ny;
     const int zm = z == 0 ? v.nz - 1 : z - 1, zp = z == v.nz - 1 ? 0 : z + 1;
-    oz[0] = (long long)(zm - z) * plane;
+    oz[0] = (zm - z) * plane;
     oz[1] = 0;
-    oz[2] = (long long)(zp - z) * plane;
+    oz[2] = (zp - z) * plane;
   }
   // offset of the node n + (dx, dy, dz)
-  __device__ __forceinline__ long long at(int dx, int dy, int dz) const {
-    return (long long)oxy[dx + 1][dy + 1] + oz[dz + 1];
+  __device__ __forceinline__ int at(int dx, int dy, int dz) const {
+    return oxy[dx + 1][dy + 1] + oz[dz + 1];
   }
 };
 

@@ -14,8 +14,10 @@ struct Launch {
 };
 
 // lattice: 0 D2Q9, 1 D3Q19; dtype: 0 F64, 1 F32, 2 F16, 3 BF16
-cudaError_t launch_step(int lattice, int dtype, const View &v, const void *fin, void *fout,
-                        const Launch &l);
+// variant: register budget of the step kernel, at least variant+1 resident
+// 256-thread blocks per SM (0..3); FP64 has a single variant.
+cudaError_t launch_step(int lattice, int dtype, int variant, const View &v, const void *fin,
+                        void *fout, const Launch &l);
 cudaError_t launch_init(int lattice, int dtype, const View &v, void *fout, double rho, double ux,
                         double uy, double uz, const Launch &l);
 cudaError_t launch_set_pop(int lattice, int dtype, const View &v, void *fout, const double *fh,

@@ -13,7 +13,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/lbm.h"
+#include "lbm.h"
 #include "geometry.hpp"
 #include "launch.hpp"
 #include "sim.hpp"
@@ -77,7 +77,9 @@ extern "C" int lbm_create(int lattice, const int dims[3], double tau, int dtype,
   if (lattice == LBM_D2Q9 && dims[2] != 1) return lbm_fail(nullptr, LBM_ERR_ARG, "D2Q9 needs nz = 1");
   const long long nxp = (dims[0] + 31) / 32 * 32;
   const long long np = nxp * dims[1] * (long long)dims[2];
-  if (np >= (1LL << 32)) return lbm_fail(nullptr, LBM_ERR_ARG, "grid too large (2^32 padded nodes)");
+  const long long Qn = lattice == LBM_D2Q9 ? 9 : 19;
+  if (np * Qn >= (1LL << 31))
+    return lbm_fail(nullptr, LBM_ERR_ARG, "grid too large: Q x padded nodes must stay below 2^31");
   lbm_sim *h = new lbm_sim();
   h->lattice = lattice;
   h->Q = lattice == LBM_D2Q9 ? 9 : 19;
@@ -132,7 +134,7 @@ extern "C" int lbm_destroy(lbm_handle h) {
   h->drop_graphs();
   h->free_geometry();
   cudaFree(h->f[0]); cudaFree(h->f[1]); cudaFree(h->flags); cudaFree(h->cbase);
-  cudaFree(h->dres); cudaFree(h->scratch);
+  cudaFree(h->dres); cudaFree(h->scratch); cudaFree(h->tiles);
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
   return LBM_OK;
@@ -154,6 +156,20 @@ extern "C" int lbm_set_options(lbm_handle h, int bc, double rho0, const double f
   if (!(rho0 > 0.0) || !std::isfinite(rho0)) return lbm_fail(h, LBM_ERR_ARG, "rho0 must be positive");
   if (h->geom_ok && h->state_ok && rho0 != h->rho0)
     return lbm_fail(h, LBM_ERR_STATE, "rho0 changes the stored shift: set it before the state");
+  if (h->geom_ok && h->state_ok && (bc == LBM_BC_BFL) != (h->bc == LBM_BC_BFL)) {
+    // BFL keeps a partial value in its written-ahead slots: re-encode the state
+    double *d = nullptr;
+    const size_t bytes = (size_t)h->N * h->Q * sizeof(double);
+    LBM_CUDA(h, cudaMalloc(&d, bytes));
+    cudaError_t e = launch_read(h->lattice, h->dtype, h->view(), h->f[h->cur], d, nullptr, nullptr,
+                                nullptr, h->aux_shape());
+    const int old_bc = h->bc;
+    h->bc = bc;
+    if (e == cudaSuccess) e = launch_set_pop(h->lattice, h->dtype, h->view(), h->f[h->cur], d, h->aux_shape());
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) { h->bc = old_bc; return lbm_fail(h, LBM_ERR_CUDA, cudaGetErrorString(e)); }
+  }
   h->bc = bc;
   h->rho0 = rho0;
   h->has_force = 0;
@@ -175,7 +191,11 @@ View lbm_sim::view() const {
   v.omega = 1.0 / tau; v.rho0 = rho0; v.qcut = qcut;
   for (int a = 0; a < 3; ++a) v.F[a] = F[a];
   v.has_force = has_force; v.has_uw = has_uw;
-  v.flags = flags; v.cbase = cbase; v.rec = rec; v.rnode = rnode;
+  v.omega_f = (float)v.omega; v.rho0_f = (float)rho0; v.qcut_f = (float)qcut;
+  for (int a = 0; a < 3; ++a) v.F_f[a] = (float)F[a];
+  v.flags = flags; v.cbase = cbase; v.rec = rec; v.rnode = rnode; v.nb = nb;
+  v.tiles = tiles; v.gx = nxp / step_bx;
+  v.ntiles = (int)ntiles; v.tpb_tiles = tiles_per_block;
   v.lq = lq; v.luw = luw; v.luw1 = luw1; v.ltag = ltag;
   return v;
 }
@@ -197,7 +217,44 @@ void lbm_sim::tune_default() {
   step_by = std::max(1, 256 / bx);
 }
 
-Launch lbm_sim::step_shape() const { return shape(step_bx, step_by); }
+Launch lbm_sim::step_shape() const {
+  Launch l;
+  l.block = dim3(step_bx, step_by, 1);
+  l.grid = dim3((unsigned)((ntiles + tiles_per_block - 1) / tiles_per_block), 1, 1);
+  l.stream = stream;
+  return l;
+}
+
+// Tile table of the step kernel for the current geometry and launch shape: for
+// each plane z, its lattice tiles {z, t} (t = tile in the plane), then its
+// boundary tiles {-1 - count, first record}.
+int lbm_sim::ensure_tiles() {
+  if (tiles && tiles_bx == step_bx && tiles_by == step_by) return LBM_OK;
+  const int tpb = step_bx * step_by;
+  const int gx = nxp / step_bx, gy = (ny + step_by - 1) / step_by;
+  std::vector<uint32_t> hc(np / 32 + 1, 0u);
+  if (nb > 0)
+    LBM_CUDA(this, cudaMemcpyAsync(hc.data(), cbase, hc.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+  LBM_CUDA(this, cudaStreamSynchronize(stream));
+  std::vector<int2> t;
+  t.reserve((size_t)nz * gx * gy + nb / tpb + nz + 1);
+  const long long pchunks = (long long)nxp * ny / 32;
+  for (int z = 0; z < nz; ++z) {
+    for (int k = 0; k < gx * gy; ++k) t.push_back(make_int2(z, k));
+    if (nb == 0) continue;
+    const long long r0 = hc[z * pchunks], r1 = hc[(z + 1) * pchunks];
+    for (long long r = r0; r < r1; r += tpb) t.push_back(make_int2(-1 - (int)std::min<long long>(tpb, r1 - r), (int)r));
+  }
+  cudaFree(tiles);
+  tiles = nullptr;
+  ntiles = (long long)t.size();
+  LBM_CUDA(this, cudaMalloc(&tiles, ntiles * sizeof(int2)));
+  LBM_CUDA(this, cudaMemcpyAsync(tiles, t.data(), ntiles * sizeof(int2), cudaMemcpyHostToDevice, stream));
+  LBM_CUDA(this, cudaStreamSynchronize(stream));
+  tiles_bx = step_bx;
+  tiles_by = step_by;
+  return LBM_OK;
+}
 Launch lbm_sim::aux_shape() const { return shape(32, 8); }
 
 // ---------------------------------------------------------------- scratch
@@ -307,8 +364,12 @@ extern "C" int lbm_get_counts(lbm_handle h, int64_t *n_fluid, int64_t *n_boundar
 
 // ---------------------------------------------------------------- stepping
 int lbm_sim::launch_steps(int n) {
+  if (n > 0) {
+    int rc = ensure_tiles();
+    if (rc) return rc;
+  }
   for (int k = 0; k < n; ++k) {
-    cudaError_t e = launch_step(lattice, dtype, view(), f[cur], f[cur ^ 1], step_shape());
+    cudaError_t e = launch_step(lattice, dtype, variant, view(), f[cur], f[cur ^ 1], step_shape());
     if (e != cudaSuccess) return lbm_fail(this, LBM_ERR_CUDA, cudaGetErrorString(e));
     cur ^= 1;
   }
@@ -338,6 +399,10 @@ extern "C" int lbm_step(lbm_handle h, int n) {
   if (!h->geom_ok || !h->state_ok) return lbm_fail(h, LBM_ERR_STATE, "set geometry and state first");
   int reps = n / lbm_sim::kGraphSteps;
   int rest = n % lbm_sim::kGraphSteps;
+  if (n > 0) {
+    int rc = h->ensure_tiles();  // never inside a capture
+    if (rc) return rc;
+  }
   if (reps > 0) {
     if (!h->graph[h->cur]) {
       int rc = h->capture(h->cur);
@@ -362,6 +427,7 @@ extern "C" int lbm_set_geometry(lbm_handle h, const uint8_t *flags, const double
 int lbm_sim::upload(const HostGeometry &g) {
   drop_graphs();
   free_geometry();
+  tiles_bx = tiles_by = 0;
   geom_ok = false;
   LBM_CUDA(this, cudaMemcpyAsync(flags, g.flags.data(), np, cudaMemcpyHostToDevice, stream));
   LBM_CUDA(this, cudaMemcpyAsync(cbase, g.cbase.data(), g.cbase.size() * sizeof(uint32_t),
@@ -431,5 +497,88 @@ int lbm_sim::download(HostGeometry &g) {
     }
   }
   LBM_CUDA(this, cudaStreamSynchronize(stream));
+  return LBM_OK;
+}
+
+// ---------------------------------------------------------------- launch configuration
+static bool valid_launch(const lbm_sim *h, int bx, int by, int variant, int tiles) {
+  if (bx < 32 || bx % 32 || h->nxp % bx || by < 1 || bx * by > 256) return false;
+  if (variant < 0 || variant > 3 || tiles < 1 || tiles > 4) return false;
+  if (h->dtype == LBM_F64 && variant != 0) return false;
+  return true;
+}
+
+extern "C" int lbm_set_launch(lbm_handle h, int bx, int by, int variant, int tiles) {
+  if (!h) return lbm_fail(nullptr, LBM_ERR_ARG, "null handle");
+  if (!valid_launch(h, bx, by, variant, tiles)) return lbm_fail(h, LBM_ERR_ARG, "invalid launch configuration");
+  h->step_bx = bx;
+  h->step_by = by;
+  h->variant = variant;
+  h->tiles_per_block = tiles;
+  h->drop_graphs();
+  return LBM_OK;
+}
+
+extern "C" int lbm_get_launch(lbm_handle h, int *bx, int *by, int *variant, int *tiles) {
+  if (!h) return lbm_fail(nullptr, LBM_ERR_ARG, "null handle");
+  if (bx) *bx = h->step_bx;
+  if (by) *by = h->step_by;
+  if (variant) *variant = h->variant;
+  if (tiles) *tiles = h->tiles_per_block;
+  return LBM_OK;
+}
+
+extern "C" int lbm_autotune(lbm_handle h, int steps, int *bx, int *by, int *variant, int *tiles,
+                            double *ms_per_step) {
+  if (!h) return lbm_fail(nullptr, LBM_ERR_ARG, "null handle");
+  if (steps < 1) return lbm_fail(h, LBM_ERR_ARG, "steps must be positive");
+  if (!h->geom_ok || !h->state_ok) return lbm_fail(h, LBM_ERR_STATE, "set geometry and state first");
+  cudaEvent_t e0, e1;
+  LBM_CUDA(h, cudaEventCreate(&e0));
+  LBM_CUDA(h, cudaEventCreate(&e1));
+  const int save[4] = {h->step_bx, h->step_by, h->variant, h->tiles_per_block};
+  int best[4] = {save[0], save[1], save[2], save[3]};
+  float best_ms = 1e30f;
+  int rc = LBM_OK;
+  const int nvar = h->dtype == LBM_F64 ? 1 : 4;
+  const int tile_opts[3] = {1, 2, 4};
+  for (int threads = 128; threads <= 256 && rc == LBM_OK; threads *= 2)
+    for (int bxx = 32; bxx <= threads && rc == LBM_OK; bxx *= 2) {
+      if (h->nxp % bxx) continue;
+      for (int var = 0; var < nvar && rc == LBM_OK; ++var)
+        for (int k = 0; k < 3 && rc == LBM_OK; ++k) {
+          h->step_bx = bxx;
+          h->step_by = threads / bxx;
+          h->variant = var;
+          h->tiles_per_block = tile_opts[k];
+          rc = h->launch_steps(2);  // warm (and build the tile table)
+          if (rc) break;
+          cudaEventRecord(e0, h->stream);
+          rc = h->launch_steps(steps);
+          cudaEventRecord(e1, h->stream);
+          if (rc) break;
+          cudaError_t e = cudaEventSynchronize(e1);
+          if (e != cudaSuccess) { rc = lbm_fail(h, LBM_ERR_CUDA, cudaGetErrorString(e)); break; }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (ms < best_ms) { best_ms = ms; best[0] = bxx; best[1] = threads / bxx; best[2] = var; best[3] = tile_opts[k]; }
+        }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) {
+    h->step_bx = save[0]; h->step_by = save[1]; h->variant = save[2]; h->tiles_per_block = save[3];
+    return rc;
+  }
+  h->step_bx = best[0];
+  h->step_by = best[1];
+  h->variant = best[2];
+  h->tiles_per_block = best[3];
+  h->drop_graphs();
+  if (bx) *bx = best[0];
+  if (by) *by = best[1];
+  if (variant) *variant = best[2];
+  if (tiles) *tiles = best[3];
+  if (ms_per_step) *ms_per_step = best_ms / steps;
   return LBM_OK;
 }

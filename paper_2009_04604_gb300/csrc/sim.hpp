@@ -42,7 +42,11 @@ struct lbm_sim {
   long long scratch_len = 0;
 
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // captured step loops, by starting buffer
-  int step_bx = 32, step_by = 8;
+  int2 *tiles = nullptr;      // step-kernel tile table (device)
+  long long ntiles = 0;
+  int tiles_bx = 0, tiles_by = 0;  // launch shape the table was built for (0: stale)
+  int tiles_per_block = 4;          // consecutive table entries per step-kernel block (1..4)
+  int step_bx = 32, step_by = 8, variant = 0;
   bool geom_ok = false, state_ok = false;
   std::string err;
 
@@ -59,6 +63,7 @@ struct lbm_sim {
   void free_geometry();
   void drop_graphs();
   int launch_steps(int n);
+  int ensure_tiles();
   int capture(int parity);
   int upload(const lbm::HostGeometry &g);
   int download(lbm::HostGeometry &g);

@@ -65,6 +65,9 @@ _SIGS = {
     "lbm_get_geometry": [ctypes.c_void_p, _u8, _d, _d, _d, _i32],
     "lbm_get_counts": [ctypes.c_void_p, _i64, _i64, _i64],
     "lbm_synchronize": [ctypes.c_void_p],
+    "lbm_set_launch": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "lbm_get_launch": [ctypes.c_void_p, _int, _int, _int, _int],
+    "lbm_autotune": [ctypes.c_void_p, ctypes.c_int, _int, _int, _int, _int, _d],
 }
 
 
@@ -253,3 +256,20 @@ class Simulation:
         a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         self._ok(self.lib.lbm_get_counts(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return a.value, b.value, c.value
+
+    def set_launch(self, bx, by, variant=0, tiles=4):
+        self._ok(self.lib.lbm_set_launch(self.h, int(bx), int(by), int(variant), int(tiles)))
+
+    def get_launch(self):
+        a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._ok(self.lib.lbm_get_launch(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                         ctypes.byref(d)))
+        return a.value, b.value, c.value, d.value
+
+    def autotune(self, steps=20):
+        """Pick the fastest step-kernel launch configuration (advances the simulation)."""
+        a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ms = ctypes.c_double()
+        self._ok(self.lib.lbm_autotune(self.h, int(steps), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                       ctypes.byref(d), ctypes.byref(ms)))
+        return dict(bx=a.value, by=b.value, variant=c.value, tiles=d.value, ms_per_step=ms.value)
