@@ -160,6 +160,30 @@ int lbm_wall_force(lbm_handle h, int tag, double F[3]);
  * Returns LBM_ERR_NONFINITE if the sum is NaN or Inf. */
 int lbm_mass(lbm_handle h, double *m);
 
+/* Capacity of the static scratch array of lbm_mass_noalloc, in per-block
+ * partial sums: 131072 doubles (1 MiB). Every GPU that loads the library holds
+ * it until the process exits. */
+#define LBM_NOALLOC_MAX_PARTIALS 131072
+
+/* Total mass, as lbm_mass computes it, without allocating device memory. The
+ * paper has no counterpart: this exists for callers that cannot call cudaMalloc.
+ * Examples are monitoring code inside a step loop that must not stall on the
+ * allocator (cudaMalloc and cudaFree can synchronise the device), and processes
+ * where another allocator already holds the device memory.
+ *   mass_dev: caller-owned device pointer to one double. The sum is written there
+ *     on the handle's stream; the call does not wait for it. Unlike lbm_mass, it
+ *     does not check the value for NaN or Inf.
+ * The per-block partial sums live in a file-scope static device array of
+ * LBM_NOALLOC_MAX_PARTIALS doubles. The reduction uses one block per 32 x 8
+ * nodes of a z-plane, (nx rounded up to 32)/32 * ceil(ny/8) * nz blocks. A
+ * lattice that needs more (above about 33.5 million padded nodes) gets
+ * LBM_ERR_ARG. The first call on a device looks up the array's device address,
+ * once per device: make that call with the handle's device current and before
+ * any stream capture. Every call reuses the same array, and each call writes
+ * every partial it reads. Calls whose work overlaps on the GPU, for instance on
+ * two streams, race on the array and give wrong sums: serialise them. */
+int lbm_mass_noalloc(lbm_handle h, double *mass_dev);
+
 /* Read back the geometry the library holds, for checks: flags[N] (lbm_node),
  * q/uw/uw1/tag per link [N*Q(*3)]. Non-wall links read 0. Any pointer may be NULL. */
 int lbm_get_geometry(lbm_handle h, uint8_t *flags, double *q, double *uw, double *uw1,

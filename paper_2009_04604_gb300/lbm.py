@@ -68,6 +68,7 @@ _SIGS = {
     "lbm_set_launch": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "lbm_get_launch": [ctypes.c_void_p, _int, _int, _int, _int],
     "lbm_autotune": [ctypes.c_void_p, ctypes.c_int, _int, _int, _int, _int, _d],
+    "lbm_mass_noalloc": [ctypes.c_void_p, ctypes.c_void_p],
 }
 
 
@@ -273,3 +274,10 @@ class Simulation:
         self._ok(self.lib.lbm_autotune(self.h, int(steps), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
                                        ctypes.byref(d), ctypes.byref(ms)))
         return dict(bx=a.value, by=b.value, variant=c.value, tiles=d.value, ms_per_step=ms.value)
+
+    def mass_noalloc(self, out):
+        """Total mass into the caller's FP64 device tensor ``out[0]``, without any device
+        allocation (static scratch; see lbm_mass_noalloc in include/lbm.h)."""
+        self._ok(self.lib.lbm_mass_noalloc(self.h, ctypes.c_void_p(out.data_ptr())))
+        self._torch.cuda.current_stream().wait_stream(self.stream)
+        return out
