@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--launch", default=None, help="bx,by,variant,tiles of the step kernel (default: autotune)")
     ap.add_argument("--tune-steps", type=int, default=20)
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP16/BF16 and batched measurements")
     return ap.parse_args()
 
 
@@ -191,6 +192,77 @@ def cores_used():
         return os.cpu_count()
 
 
+# ---------------------------------------------------------------- extra measurements
+def time_steps(torch, stream, fn, steps):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn(steps)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def dtype_variant(torch, lbm, W, dtype, steps, peak):
+    """The same sphere-duct workload with another storage type (autotuned)."""
+    wl = W.sphere_duct()
+    s = lbm.Simulation(wl["lattice"], wl["dims"], wl["tau"], dtype)
+    s.set_options("elibb_f", wl["rho0"], wl["force"], wl["xshift"])
+    s.build_geometry(wl["base"], wl["base_u"], wl["shapes"])
+    s.init(wl["rho0"])
+    tuned = s.autotune(10)
+    s.step(10)
+    ms = time_steps(torch, s.stream, s.step, steps)
+    nfluid, nb, nl = s.counts()
+    np_ = (wl["dims"][0] + 31) // 32 * 32 * wl["dims"][1] * wl["dims"][2]
+    abytes = algorithmic_bytes(nfluid, np_, nb, nl, 19, DTYPE_BYTES[dtype], 8 if dtype == "f64" else 4, False)
+    ach = abytes / (ms / steps * 1e-3) / 1e9
+    s.close()
+    return {"value": round(nfluid * steps / (ms * 1e-3) / 1e6, 2), "unit": "MLUPS", "steps": steps,
+            "roofline_frac": round(ach / peak, 4), "achieved_gbs": round(ach, 1), "launch": tuned}
+
+
+def batched_vs_plain(torch, lbm, W, regime, dtype, steps):
+    """Batched configuration: many D3Q19 ducts, one launch per step for all (graph
+    replay) against one launch per simulation per step. The per-node code is the
+    same, so both give identical results (tested bit for bit)."""
+    if regime == "large":
+        wls = W.batched_ducts()
+    else:
+        wls = W.batched_ducts(lo=16, hi=48, target=None, rmin=2.0, rmax=6.0)
+    st = torch.cuda.Stream()
+    sims = []
+    for wl in wls:
+        s = lbm.Simulation(wl["lattice"], wl["dims"], wl["tau"], dtype, stream=st)
+        s.set_options("elibb_f", wl["rho0"], wl["force"], wl["xshift"])
+        s.build_geometry(wl["base"], wl["base_u"], wl["shapes"])
+        s.init(wl["rho0"])
+        sims.append(s)
+    nfluid = sum(s.counts()[0] for s in sims)
+    b = lbm.Batch(sims)
+    tuned = b.autotune(4)
+    b.step(4)
+    ms_b = time_steps(torch, st, b.step, steps)
+    for s in sims:  # the plain form uses the batch's launch configuration
+        s.set_launch(tuned["bx"], tuned["by"], tuned["variant"], tuned["tiles"])
+
+    def plain(n):
+        for _ in range(n):
+            for s in sims:
+                s.step(1)
+    plain(2)
+    ms_p = time_steps(torch, st, plain, steps)
+    b.close()
+    for s in sims:
+        s.close()
+    vb = nfluid * steps / (ms_b * 1e-3) / 1e6
+    vp = nfluid * steps / (ms_p * 1e-3) / 1e6
+    return {"sims": len(wls), "nodes": int(sum(int(np.prod(w["dims"])) for w in wls)), "nfluid": nfluid,
+            "dtype": dtype, "steps": steps, "batched_mlups": round(vb, 1), "plain_mlups": round(vp, 1),
+            "speedup": round(vb / vp, 3), "launch": tuned}
+
+
 # ---------------------------------------------------------------- arms
 def reference_arm(args, rank, dist):
     from paper_2009_04604_gb300 import workloads as W
@@ -301,6 +373,19 @@ def ours_arm(args, rank, world, dist):
     _, u = s.macros()
     finite = bool(torch.isfinite(u).all().item())
     s.close()
+    extras = {}
+    if not args.no_extras:
+        for dt in ("f16", "bf16"):
+            if dt != args.dtype:
+                try:
+                    extras[dt] = dtype_variant(torch, lbm, W, dt, min(args.steps, 400), peak)
+                except Exception as exc:
+                    extras[dt] = {"error": str(exc)[:200]}
+        for regime, st_ in (("large", 100), ("small", 400)):
+            try:
+                extras["batched_" + regime] = batched_vs_plain(torch, lbm, W, regime, "f32", st_)
+            except Exception as exc:
+                extras["batched_" + regime] = {"error": str(exc)[:200]}
     if rank != 0:
         return 0
     line = {
@@ -323,6 +408,7 @@ def ours_arm(args, rank, world, dist):
         "gpu_launches": args.steps,
         "cpu_baseline": cpu,
         "state_finite": finite,
+        "variants": extras,
     }
     print(json.dumps(line), flush=True)
     return 0

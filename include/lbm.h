@@ -214,6 +214,36 @@ int lbm_get_launch(lbm_handle h, int *bx, int *by, int *variant, int *tiles);
 int lbm_autotune(lbm_handle h, int steps, int *bx, int *by, int *variant, int *tiles,
                  double *ms_per_step);
 
+/* ---- Batches: many independent simulations advanced by one launch per step ----
+ * The simulations of a batch share one lattice, one storage type and one stream,
+ * and each keeps its own geometry, parameters and state. A batched step runs the
+ * same per-node code as lbm_step, so each simulation gets exactly the results it
+ * would get alone. The blocks of the launch take the tiles of every simulation
+ * (lattice tiles and boundary-record tiles, plane by plane), and the steps replay
+ * from captured CUDA graphs. This is for workloads of many small or uneven grids,
+ * where one launch per simulation would leave the GPU idle between launches. The
+ * handles stay usable on their own; lbm_batch_step picks up their current state. */
+typedef struct lbm_batch_s *lbm_batch;
+
+/* sims: n distinct handles, each with geometry and state, all with the same
+ * lattice, dtype and stream. Returns LBM_ERR_ARG or LBM_ERR_STATE otherwise. The
+ * batch does not own the handles: destroy the batch first. */
+int lbm_batch_create(const lbm_handle *sims, int n, lbm_batch *out);
+int lbm_batch_destroy(lbm_batch b);
+
+/* Enqueue n steps of every simulation of the batch on the shared stream. */
+int lbm_batch_step(lbm_batch b, int n);
+
+/* Launch configuration and autotuner of the batched step, as lbm_set_launch and
+ * lbm_autotune. bx must divide the padded row length of every simulation. The
+ * autotuner advances every simulation by its trial steps. */
+int lbm_batch_set_launch(lbm_batch b, int bx, int by, int variant, int tiles);
+int lbm_batch_autotune(lbm_batch b, int steps, int *bx, int *by, int *variant, int *tiles,
+                       double *ms_per_step);
+
+/* Message of the last error on a batch. */
+const char *lbm_batch_last_error(lbm_batch b);
+
 /* Wait for all work on the handle's stream. */
 int lbm_synchronize(lbm_handle h);
 

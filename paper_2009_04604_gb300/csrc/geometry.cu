@@ -406,6 +406,7 @@ extern "C" int lbm_build_geometry(lbm_handle h, const uint8_t *base, const doubl
   const long long nblk = (nchunk + 1023) / 1024;
   GeoView g;
   cudaStream_t st = h->stream;
+  ++h->version;
   h->drop_graphs();
   h->free_geometry();
   h->tiles_bx = h->tiles_by = 0;

@@ -410,6 +410,44 @@ __global__ void __launch_bounds__(256, MINB) k_step(const View v, const S *__res
   }
 }
 
+// ---------------------------------------------------------------- batched step
+// Many independent simulations advance in one launch. Entry k holds the view
+// and the two population buffers of simulation k. The tile table lists
+// {sim, z, t, 0} lattice tiles and {sim, -1, first, count} boundary tiles, one
+// simulation after another, each plane-interleaved as in k_step. parity picks
+// which buffer of each entry is read in this step. A block copies the entry of
+// its tile into shared memory. The per-node code is the same as k_step's,
+// including the per-simulation choice of the force path. A batched simulation
+// therefore gives exactly the results it gives when stepped alone.
+struct BatchEntry {
+  View v;
+  const void *f0;  // read on even batch steps
+  void *f1;        // read on odd batch steps
+};
+
+template <class L, typename S, typename M, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_step_batch(const BatchEntry *__restrict__ entries,
+                                                          const int4 *__restrict__ tiles, int ntiles,
+                                                          int T, int parity) {
+  __shared__ M stage[L::Q * 256];
+  __shared__ BatchEntry se;
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  for (int k = 0; k < T; ++k) {
+    const int idx = blockIdx.x * T + k;
+    if (idx >= ntiles) break;  // uniform across the block
+    const int4 tile = tiles[idx];
+    __syncthreads();  // the previous tile is done with se
+    if (t == 0) se = entries[tile.x];
+    __syncthreads();
+    const S *fin = static_cast<const S *>(parity ? se.f1 : se.f0);
+    S *fout = static_cast<S *>(parity ? const_cast<void *>(se.f0) : se.f1);
+    // each simulation takes the same compiled path as when it steps alone
+    if (tile.y < 0) boundary_tile<L, S, M>(se.v, fin, fout, make_int2(-1 - tile.w, tile.z), stage);
+    else if (se.v.has_force) lattice_tile<L, S, M, true>(se.v, fin, fout, make_int2(tile.y, tile.z));
+    else lattice_tile<L, S, M, false>(se.v, fin, fout, make_int2(tile.y, tile.z));
+  }
+}
+
 // ---------------------------------------------------------------- state set-up and read-out
 // f_i(x) = f^eq_i(rho, u) on every fluid node, written to the slot its gather reads.
 template <class L, typename S, typename M>

@@ -180,6 +180,7 @@ extern "C" int lbm_set_options(lbm_handle h, int bc, double rho0, const double f
   if (h->lattice == LBM_D2Q9) { h->F[2] = 0.0; }
   h->xshift = xshift;
   h->drop_graphs();
+  ++h->version;
   return LBM_OK;
 }
 
@@ -425,6 +426,7 @@ extern "C" int lbm_set_geometry(lbm_handle h, const uint8_t *flags, const double
 }
 
 int lbm_sim::upload(const HostGeometry &g) {
+  ++version;
   drop_graphs();
   free_geometry();
   tiles_bx = tiles_by = 0;

@@ -48,6 +48,7 @@ struct lbm_sim {
   int tiles_per_block = 4;          // consecutive table entries per step-kernel block (1..4)
   int step_bx = 32, step_by = 8, variant = 0;
   bool geom_ok = false, state_ok = false;
+  int version = 0;  // bumped whenever the kernel view changes (options, geometry)
   std::string err;
 
   size_t elem_size() const;

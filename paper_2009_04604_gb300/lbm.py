@@ -69,6 +69,11 @@ _SIGS = {
     "lbm_get_launch": [ctypes.c_void_p, _int, _int, _int, _int],
     "lbm_autotune": [ctypes.c_void_p, ctypes.c_int, _int, _int, _int, _int, _d],
     "lbm_mass_noalloc": [ctypes.c_void_p, ctypes.c_void_p],
+    "lbm_batch_create": [P(ctypes.c_void_p), ctypes.c_int, P(ctypes.c_void_p)],
+    "lbm_batch_destroy": [ctypes.c_void_p],
+    "lbm_batch_step": [ctypes.c_void_p, ctypes.c_int],
+    "lbm_batch_set_launch": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "lbm_batch_autotune": [ctypes.c_void_p, ctypes.c_int, _int, _int, _int, _int, _d],
 }
 
 
@@ -91,6 +96,8 @@ def load():
             fn.restype = ctypes.c_int
         lib.lbm_last_error.argtypes = [ctypes.c_void_p]
         lib.lbm_last_error.restype = ctypes.c_char_p
+        lib.lbm_batch_last_error.argtypes = [ctypes.c_void_p]
+        lib.lbm_batch_last_error.restype = ctypes.c_char_p
         _lib = lib
     return _lib
 
@@ -281,3 +288,45 @@ class Simulation:
         self._ok(self.lib.lbm_mass_noalloc(self.h, ctypes.c_void_p(out.data_ptr())))
         self._torch.cuda.current_stream().wait_stream(self.stream)
         return out
+
+
+class Batch:
+    """Many simulations (same lattice, dtype and stream) advanced by one launch per step."""
+
+    def __init__(self, sims):
+        self.lib = load()
+        self.sims = list(sims)
+        arr = (ctypes.c_void_p * len(self.sims))(*[s.h.value for s in self.sims])
+        b = ctypes.c_void_p()
+        rc = self.lib.lbm_batch_create(arr, len(self.sims), ctypes.byref(b))
+        if rc != 0:
+            raise LBMError(rc, "lbm_batch_create rejected the simulations (lattice, dtype, stream or state)")
+        self.b = b
+
+    def _ok(self, rc):
+        if rc != 0:
+            raise LBMError(rc, self.lib.lbm_batch_last_error(self.b).decode())
+
+    def step(self, n=1):
+        self._ok(self.lib.lbm_batch_step(self.b, int(n)))
+
+    def set_launch(self, bx, by, variant=0, tiles=1):
+        self._ok(self.lib.lbm_batch_set_launch(self.b, int(bx), int(by), int(variant), int(tiles)))
+
+    def autotune(self, steps=10):
+        a, b_, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ms = ctypes.c_double()
+        self._ok(self.lib.lbm_batch_autotune(self.b, int(steps), ctypes.byref(a), ctypes.byref(b_), ctypes.byref(c),
+                                             ctypes.byref(d), ctypes.byref(ms)))
+        return dict(bx=a.value, by=b_.value, variant=c.value, tiles=d.value, ms_per_step=ms.value)
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

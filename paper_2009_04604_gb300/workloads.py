@@ -187,3 +187,50 @@ def random_geometry(dims, seed=0, solid_frac=0.15, open_frac=0.02, Q=19, moving=
     uw1 = uw + 0.001 * rng.standard_normal((N, Q, 3)) if moving else None
     tag = rng.integers(0, 8, (N, Q)).astype(np.int32)
     return flags, q, uw, uw1, tag
+
+
+def batched_ducts(n=96, lo=48, hi=192, target=1.2e8, tol=0.05, seed=11, rmin=6.0, rmax=20.0,
+                  u_lo=0.005, u_hi=0.03, tau=0.7, max_draws=10000):
+    """n independent D3Q19 ducts of uneven sizes (the batched configuration).
+
+    Each axis is drawn uniformly from {lo..hi}. Independent draws average
+    96 * 120^3 = 1.66e8 nodes, so a total near the 1.2e8 target is very unlikely.
+    While the total exceeds target*(1 + tol), one randomly chosen duct is
+    redrawn, and the draw is kept when it brings the total down. This keeps every
+    axis in {lo..hi} and ends within target*(1 +- tol). A target of None keeps
+    the first draw. Each duct holds a sphere or an axis-aligned
+    ellipsoid with semi-axes in [rmin, rmax], clamped to fit, at a random interior
+    position at least 4 nodes from the walls, and gets an inlet speed in
+    [u_lo, u_hi]. Returns a list of workload dicts."""
+    rng = np.random.default_rng(seed)
+    dims = rng.integers(lo, hi + 1, size=(n, 3))
+    vol = np.prod(dims, axis=1)
+    for _ in range(max_draws):
+        if target is None or vol.sum() <= target * (1 + tol):
+            break
+        j = int(rng.integers(n))
+        d = rng.integers(lo, hi + 1, size=3)
+        if np.prod(d) < vol[j]:
+            dims[j] = d
+            vol[j] = np.prod(d)
+    out = []
+    for j in range(n):
+        d = tuple(int(v) for v in dims[j])
+        u_in = float(rng.uniform(u_lo, u_hi))
+        room = (min(d) - 2) / 2.0 - 4.0
+        if rng.random() < 0.5:
+            r = float(np.clip(rng.uniform(rmin, rmax), 1.0, max(1.0, room)))
+            axes = (r, r, r)
+            kind = "sphere"
+        else:
+            axes = tuple(float(np.clip(rng.uniform(rmin, rmax), 1.0, max(1.0, (d[a] - 2) / 2.0 - 4.0)))
+                         for a in range(3))
+            kind = "ellipsoid"
+        c = tuple(float(rng.uniform(1 + axes[a] + 4, d[a] - 2 - axes[a] - 4)) if d[a] - 2 - axes[a] - 4 > 1 + axes[a] + 4
+                  else (d[a] - 1) / 2.0 for a in range(3))
+        base, base_u = duct_base(d, u_in)
+        shape = dict(type="sphere", tag=1, c=c, r=(axes[0], 0, 0)) if kind == "sphere" else \
+            dict(type="ellipsoid", tag=1, c=c, r=axes)
+        out.append(dict(lattice=D3Q19, dims=d, tau=tau, xshift=0, force=(0.0, 0.0, 0.0), base=base,
+                        base_u=base_u, shapes=[shape], rho0=1.0, u_in=u_in))
+    return out
