@@ -131,6 +131,23 @@ int lbm_set_geometry(lbm_handle h, const uint8_t *flags, const double *q, const 
 int lbm_build_geometry(lbm_handle h, const uint8_t *base, const double *base_u,
                        const lbm_shape *shapes, int nshapes);
 
+/* A rigid body moving on a prescribed trajectory: a sphere or an axis-aligned
+ * ellipsoid (body->type, r, tag; its c, v and om fields are ignored).
+ *   traj[ntraj*9] (host, FP64): for pose k, the centre c[3], velocity v[3] and
+ *     angular velocity om[3]. Step t uses pose (t0 + t) mod ntraj, so a periodic
+ *     path needs one period of poses.
+ * After every step the library rebuilds the body's link geometry on the device
+ * (the link-geometry kernel, restricted to a region box that covers the whole
+ * trajectory): node kinds, q and u_w = v + om x (x_W - c) at the new pose, and
+ * u_w at the following pose for the wall population at s = 0 (Sec. II.D-II.E).
+ * A node that turns fluid gets f^eq(rho0, u_body) (the paper refills by local
+ * iterations, App. D). A node that turns solid is dropped. The region, widened
+ * by one node, must lie inside the lattice and hold only fluid nodes of the
+ * static geometry; otherwise LBM_ERR_ARG. BFL is not available with a moving
+ * body. Call after lbm_build_geometry/lbm_set_geometry; a new static geometry
+ * removes the body. lbm_wall_force includes the body's links (its tag). */
+int lbm_set_moving_body(lbm_handle h, const lbm_shape *body, const double *traj, int ntraj, int t0);
+
 /* Equilibrium start f = f^eq(rho, u) on every fluid node. */
 int lbm_init(lbm_handle h, double rho, const double u[3]);
 
@@ -226,8 +243,9 @@ int lbm_autotune(lbm_handle h, int steps, int *bx, int *by, int *variant, int *t
 typedef struct lbm_batch_s *lbm_batch;
 
 /* sims: n distinct handles, each with geometry and state, all with the same
- * lattice, dtype and stream. Returns LBM_ERR_ARG or LBM_ERR_STATE otherwise. The
- * batch does not own the handles: destroy the batch first. */
+ * lattice, dtype and stream, none with a moving body. Returns LBM_ERR_ARG or
+ * LBM_ERR_STATE otherwise. The batch does not own the handles: destroy the batch
+ * first. */
 int lbm_batch_create(const lbm_handle *sims, int n, lbm_batch *out);
 int lbm_batch_destroy(lbm_batch b);
 

@@ -173,6 +173,7 @@ extern "C" int lbm_batch_create(const lbm_handle *sims, int n, lbm_batch *out) {
     lbm_sim *s = sims[k];
     if (!s) { delete b; return LBM_ERR_ARG; }
     if (!s->geom_ok || !s->state_ok) { delete b; return LBM_ERR_STATE; }
+    if (s->mb.on) { delete b; return LBM_ERR_ARG; }  // moving bodies step alone
     if (k == 0) {
       b->lattice = s->lattice;
       b->dtype = s->dtype;
@@ -219,8 +220,10 @@ extern "C" int lbm_batch_step(lbm_batch b, int n) {
   if (!b) return LBM_ERR_ARG;
   if (n < 0) return bfail(b, LBM_ERR_ARG, "negative step count");
   if (n == 0) return LBM_OK;
-  for (lbm_sim *s : b->sims)
+  for (lbm_sim *s : b->sims) {
     if (!s->geom_ok || !s->state_ok) return bfail(b, LBM_ERR_STATE, "a simulation lost its geometry or state");
+    if (s->mb.on) return bfail(b, LBM_ERR_ARG, "a simulation with a moving body cannot be batched");
+  }
   if (!entries_current(b)) {
     int rc = build_batch(b);
     if (rc) return rc;

@@ -16,11 +16,14 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <string>
 #include <vector>
 
 #include "lbm.h"
 #include "geometry.hpp"
+#include "kernels.cuh"
+#include "launch.hpp"
 #include "sim.hpp"
 
 namespace lbm {
@@ -307,6 +310,8 @@ __global__ void k_geo_fill(const GeoView g, const uint32_t *__restrict__ cbase,
 
 using namespace lbm;
 
+void exclusive_scan(uint32_t *a, long long n, uint32_t *tot, uint32_t *total, cudaStream_t st);
+
 #define GEO_CUDA(call)                                                                          \
   do {                                                                                          \
     cudaError_t e_ = (call);                                                                    \
@@ -315,6 +320,14 @@ using namespace lbm;
                     std::string(#call) + ": " + cudaGetErrorString(e_));                        \
       goto done;                                                                                \
     }                                                                                           \
+  } while (0)
+
+#define LBM_CUDA_GEO(h, call)                                                                   \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return lbm_fail((h), e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,        \
+                      std::string(#call) + ": " + cudaGetErrorString(e_));                      \
   } while (0)
 
 static void shape_box(const lbm_shape &s, int D, double lo[3], double hi[3], bool &bounded) {
@@ -326,7 +339,7 @@ static void shape_box(const lbm_shape &s, int D, double lo[3], double hi[3], boo
   }
 }
 
-static void exclusive_scan(uint32_t *a, long long n, uint32_t *tot, uint32_t *total, cudaStream_t st) {
+void exclusive_scan(uint32_t *a, long long n, uint32_t *tot, uint32_t *total, cudaStream_t st) {
   const long long nblk = (n + 1023) / 1024;
   k_scan_block<<<(unsigned)nblk, 1024, 0, st>>>(a, n, tot);
   k_scan_totals<<<1, 1, 0, st>>>(tot, nblk, total);
@@ -407,6 +420,7 @@ extern "C" int lbm_build_geometry(lbm_handle h, const uint8_t *base, const doubl
   GeoView g;
   cudaStream_t st = h->stream;
   ++h->version;
+  h->free_moving_body();
   h->drop_graphs();
   h->free_geometry();
   h->tiles_bx = h->tiles_by = 0;
@@ -496,4 +510,354 @@ done:
   cudaFree(d_base); cudaFree(d_base_u); cudaFree(d_shapes); cudaFree(d_cstart); cudaFree(d_items);
   cudaFree(crec); cudaFree(clink); cudaFree(tot); cudaFree(totals);
   return rc;
+}
+
+// ====================================================================== moving body
+// A rigid body on a prescribed trajectory (Sec. II.E: wall velocity at the link's
+// wall point). After every step t -> t+1, inside the fixed region box that covers
+// the body's whole trajectory:
+//  1. k_move_update: node kinds for the pose at t+1. A node that turns fluid
+//     (solid at t, fluid at t+1) is refilled with f^eq(rho0, u_body(x)). Its
+//     gather slots are written in the buffer the next step reads. The paper
+//     refills by local iterations (App. D); the equilibrium refill is this
+//     library's simpler choice.
+//  2. k_move_count, scan, k_move_fill: the boundary records of the region's
+//     fluid nodes, with q and u_w at t+1 and u_w at t+2, in region order.
+//  3. k_move_advance: the pose index moves on.
+// Everything stays on the device, so the step loop remains one CUDA graph.
+namespace lbm {
+
+struct MoveGeo {
+  View v;
+  int D;
+  const GeoShape *shape;   // the body at unit pose: centre and velocities come from traj
+  const double *traj;      // [ntraj][9]
+  int ntraj;
+  const int *step;         // current pose index
+  int ox, oy, oz, rx, ry, rz;
+  long long rsize;
+};
+
+__device__ __forceinline__ GeoShape body_at(const MoveGeo &g, int k) {
+  GeoShape s = *g.shape;
+  const double *p = g.traj + 9LL * (k % g.ntraj);
+  const double *p1 = g.traj + 9LL * ((k + 1) % g.ntraj);
+  for (int a = 0; a < 3; ++a) {
+    s.c[a] = p[a]; s.v[a] = p[3 + a]; s.om[a] = p[6 + a];
+    s.v1[a] = p1[3 + a]; s.om1[a] = p1[6 + a];
+  }
+  return s;
+}
+
+__device__ __forceinline__ void region_xyz(const MoveGeo &g, long long r, int &x, int &y, int &z) {
+  x = g.ox + (int)(r % g.rx);
+  y = g.oy + (int)((r / g.rx) % g.ry);
+  z = g.oz + (int)(r / ((long long)g.rx * g.ry));
+}
+
+template <class L, typename S, typename M>
+__global__ void k_move_update(const MoveGeo g, int koff, int refill, uint8_t *__restrict__ flags,
+                              S *__restrict__ fout) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= g.rsize) return;
+  int x, y, z;
+  region_xyz(g, r, x, y, z);
+  const View &v = g.v;
+  const int n = (z * v.ny + y) * v.nxp + x;
+  const GeoShape b = body_at(g, *g.step + koff);
+  const uint8_t old = flags[n] & 3;
+  const uint8_t now = shape_solid(b, g.D, (double)x, (double)y, (double)z) ? K_SOLID : K_FLUID;
+  if (refill && old != K_FLUID && now == K_FLUID) {
+    // u_body at the node at the new pose: v + om x (x - c)
+    const double rx_ = x - b.c[0], ry_ = y - b.c[1], rz_ = g.D == 3 ? z - b.c[2] : 0.0;
+    double u[3] = {b.v[0] + b.om[1] * rz_ - b.om[2] * ry_, b.v[1] + b.om[2] * rx_ - b.om[0] * rz_,
+                   b.v[2] + b.om[0] * ry_ - b.om[1] * rx_};
+    if (g.D == 2) u[2] = 0.0;
+    const M ux = M(u[0]), uy = M(u[1]), uz = M(u[2]);
+    const M usq = ux * ux + uy * uy + uz * uz;
+    Nbr nb;
+    nb.init(v, x, y, z);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+      fout[(long long)i * v.np + n + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))] =
+          to_store<S, M>(feq_s<L, M>(i, M(0), M(v.rho0), ux, uy, uz, usq));
+  }
+  flags[n] = now;
+}
+
+// per 32-node region chunk: records and wall links (the region's fluid nodes whose
+// upstream neighbours are solid)
+template <class L>
+__global__ void k_move_count(const MoveGeo g, const uint8_t *__restrict__ flags, uint32_t *__restrict__ crec,
+                             uint32_t *__restrict__ clink, long long rpad) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rpad) return;  // rpad is a multiple of 32: whole warps
+  uint32_t cut = 0;
+  if (r < g.rsize) {
+    int x, y, z;
+    region_xyz(g, r, x, y, z);
+    const View &v = g.v;
+    const int n = (z * v.ny + y) * v.nxp + x;
+    if ((flags[n] & 3) == K_FLUID) {
+      Nbr nb;
+      nb.init(v, x, y, z);
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        if (L::cx(i) == 0 && L::cy(i) == 0 && L::cz(i) == 0) continue;
+        if ((flags[n + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))] & 3) == K_SOLID) cut |= 1u << i;
+      }
+    }
+  }
+  const uint32_t bal = __ballot_sync(0xffffffffu, cut != 0);
+  uint32_t nl = __popc(cut);
+  for (int o = 16; o > 0; o >>= 1) nl += __shfl_down_sync(0xffffffffu, nl, o);
+  if ((threadIdx.x & 31) == 0) {
+    crec[r >> 5] = __popc(bal);
+    clink[r >> 5] = nl;
+  }
+}
+
+template <class L, typename LT>
+__global__ void k_move_fill(const MoveGeo g, int koff, const uint8_t *__restrict__ flags,
+                            const uint32_t *__restrict__ cbase, const uint32_t *__restrict__ lbase,
+                            long long rpad, Rec *__restrict__ rec, uint32_t *__restrict__ rnode,
+                            LT *__restrict__ lq, LT *__restrict__ luw, LT *__restrict__ luw1,
+                            uint8_t *__restrict__ ltag) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rpad) return;
+  const View &v = g.v;
+  int x = 0, y = 0, z = 0, n = 0;
+  Rec rc = {0u, 0u, 0u, 0u};
+  Nbr nb;
+  if (r < g.rsize) {
+    region_xyz(g, r, x, y, z);
+    n = (z * v.ny + y) * v.nxp + x;
+    if ((flags[n] & 3) == K_FLUID) {
+      nb.init(v, x, y, z);
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        if (L::cx(i) == 0 && L::cy(i) == 0 && L::cz(i) == 0) continue;
+        if ((flags[n + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))] & 3) == K_SOLID) rc.cut |= 1u << i;
+      }
+    }
+  }
+  const uint32_t bal = __ballot_sync(0xffffffffu, rc.cut != 0);
+  const uint32_t cnt = __popc(rc.cut);
+  uint32_t s = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) >= o) s += t;
+  }
+  if (!rc.cut) return;
+  const uint32_t lt = (1u << (threadIdx.x & 31)) - 1u;
+  const uint32_t rid = cbase[r >> 5] + __popc(bal & lt);
+  rc.link0 = lbase[r >> 5] + s - cnt;
+  const GeoShape b = body_at(g, *g.step + koff);
+  const double X[3] = {(double)x, (double)y, (double)z};
+  bool moving = false;
+  uint32_t li = rc.link0;
+  for (int i = 0; i < L::Q; ++i) {
+    if (!(rc.cut & (1u << i))) continue;
+    const int c[3] = {L::cx(i), L::cy(i), L::cz(i)};
+    double qq = shape_cross(b, g.D, X, c);
+    if (qq <= 0.0) qq = 1.0;  // rounding at a tangent: the wall sits on the solid node
+    double rr[3];
+    for (int a = 0; a < 3; ++a) rr[a] = a < g.D ? X[a] - qq * c[a] - b.c[a] : 0.0;
+    double u0[3] = {b.v[0] + b.om[1] * rr[2] - b.om[2] * rr[1], b.v[1] + b.om[2] * rr[0] - b.om[0] * rr[2],
+                    b.v[2] + b.om[0] * rr[1] - b.om[1] * rr[0]};
+    double u1[3] = {b.v1[0] + b.om1[1] * rr[2] - b.om1[2] * rr[1], b.v1[1] + b.om1[2] * rr[0] - b.om1[0] * rr[2],
+                    b.v1[2] + b.om1[0] * rr[1] - b.om1[1] * rr[0]};
+    if (g.D == 2) { u0[2] = 0.0; u1[2] = 0.0; }
+    for (int a = 0; a < 3; ++a) {
+      if (u0[a] != 0.0 || u1[a] != 0.0) moving = true;
+      luw[3 * li + a] = (LT)u0[a];
+      luw1[3 * li + a] = (LT)u1[a];
+    }
+    lq[li] = (LT)qq;
+    ltag[li] = (uint8_t)b.tag;
+    ++li;
+  }
+  if (moving) rc.open |= REC_MOVING;
+  rec[rid] = rc;
+  rnode[rid] = (uint32_t)n;
+}
+
+__global__ void k_move_advance(int *step) { *step += 1; }
+
+template <class Fn>
+static cudaError_t move_dispatch(int lattice, int dtype, Fn &&fn) {
+  if (lattice == 0) {
+    switch (dtype) {
+      case 0: return fn.template operator()<D2Q9, double, double>();
+      case 1: return fn.template operator()<D2Q9, float, float>();
+      case 2: return fn.template operator()<D2Q9, __half, float>();
+      default: return fn.template operator()<D2Q9, __nv_bfloat16, float>();
+    }
+  }
+  switch (dtype) {
+    case 0: return fn.template operator()<D3Q19, double, double>();
+    case 1: return fn.template operator()<D3Q19, float, float>();
+    case 2: return fn.template operator()<D3Q19, __half, float>();
+    default: return fn.template operator()<D3Q19, __nv_bfloat16, float>();
+  }
+}
+
+// Body geometry of pose (*step + koff) into record set `set`; refill fresh nodes in fout.
+static cudaError_t move_geometry(lbm_sim *h, int koff, int refill, void *fout, int set) {
+  MovingBody &mb = h->mb;
+  MoveGeo g;
+  g.v = h->view();
+  g.D = h->lattice == LBM_D2Q9 ? 2 : 3;
+  g.shape = static_cast<const GeoShape *>(mb.shape);
+  g.traj = mb.traj;
+  g.ntraj = mb.ntraj;
+  g.step = mb.step;
+  g.ox = mb.ox; g.oy = mb.oy; g.oz = mb.oz; g.rx = mb.rx; g.ry = mb.ry; g.rz = mb.rz;
+  g.rsize = mb.rsize;
+  cudaStream_t st = h->stream;
+  const unsigned blocks = (unsigned)((mb.rpad + 255) / 256);
+  const long long nchunk = mb.rpad / 32;
+  return move_dispatch(h->lattice, h->dtype, [&]<class L, typename S, typename M>() {
+    k_move_update<L, S, M><<<blocks, 256, 0, st>>>(g, koff, refill, h->flags, static_cast<S *>(fout));
+    k_move_count<L><<<blocks, 256, 0, st>>>(g, h->flags, mb.crec, mb.clink, mb.rpad);
+    exclusive_scan(mb.crec, nchunk, mb.tot, reinterpret_cast<uint32_t *>(mb.count[set]), st);
+    exclusive_scan(mb.clink, nchunk, mb.tot, mb.totals, st);
+    k_move_fill<L, M><<<blocks, 256, 0, st>>>(g, koff, h->flags, mb.crec, mb.clink, mb.rpad, mb.rec[set],
+                                              mb.rnode[set], static_cast<M *>(mb.lq[set]),
+                                              static_cast<M *>(mb.luw[set]), static_cast<M *>(mb.luw1[set]),
+                                              mb.ltag[set]);
+    return cudaGetLastError();
+  });
+}
+
+}  // namespace lbm
+
+int lbm_sim::move_after_step(void *fout, int set) {
+  // The body's momentum exchange of the step just taken (its records are set ^ 1).
+  // It is taken before the refill, which may overwrite the outgoing populations
+  // f*_ibar(x_F, t) of links whose solid node turns fluid.
+  const int s = set ^ 1;
+  const RecSet rs{mb.rec[s], mb.rnode[s], mb.lq[s], mb.luw[s], mb.luw1[s], mb.ltag[s]};
+  Launch lf;
+  lf.grid = dim3((unsigned)mb.nfpart);
+  lf.block = dim3(256);
+  lf.stream = stream;
+  cudaError_t e = launch_force(lattice, dtype, view(), fout, rs, 0, mb.count[s], -1, mb.fpart, lf);
+  if (e == cudaSuccess) e = move_geometry(this, 1, 1, fout, set);
+  if (e == cudaSuccess) {
+    k_move_advance<<<1, 1, 0, stream>>>(mb.step);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return lbm_fail(this, LBM_ERR_CUDA, std::string("moving body: ") + cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+void lbm_sim::free_moving_body() {
+  if (!mb.on && !mb.traj) return;
+  cudaStreamSynchronize(stream);
+  cudaFree(mb.shape); cudaFree(mb.traj); cudaFree(mb.step); cudaFree(mb.fpart);
+  cudaFree(mb.crec); cudaFree(mb.clink); cudaFree(mb.tot); cudaFree(mb.totals);
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(mb.rec[k]); cudaFree(mb.rnode[k]); cudaFree(mb.lq[k]); cudaFree(mb.luw[k]); cudaFree(mb.luw1[k]);
+    cudaFree(mb.ltag[k]); cudaFree(mb.count[k]);
+  }
+  mb = MovingBody();
+  tiles_bx = tiles_by = 0;
+  drop_graphs();
+}
+
+extern "C" int lbm_set_moving_body(lbm_handle h, const lbm_shape *body, const double *traj, int ntraj, int t0) {
+  if (!h || !body || !traj) return lbm_fail(h, LBM_ERR_ARG, "null argument");
+  if (!h->geom_ok) return lbm_fail(h, LBM_ERR_STATE, "build the static geometry first");
+  if (body->type != LBM_SHAPE_SPHERE && body->type != LBM_SHAPE_ELLIPSOID)
+    return lbm_fail(h, LBM_ERR_ARG, "a moving body is a sphere or an ellipsoid");
+  if (body->tag < 0 || body->tag > 7) return lbm_fail(h, LBM_ERR_ARG, "tags must be 0..7");
+  if (ntraj < 2 || t0 < 0) return lbm_fail(h, LBM_ERR_ARG, "the trajectory needs at least two poses");
+  if (h->bc == LBM_BC_BFL) return lbm_fail(h, LBM_ERR_ARG, "BFL cannot be used with a moving body");
+  const int D = h->lattice == LBM_D2Q9 ? 2 : 3;
+  double ext[3];
+  for (int a = 0; a < 3; ++a) ext[a] = body->type == LBM_SHAPE_ELLIPSOID ? body->r[a] : body->r[0];
+  // region: the trajectory's bounding box, widened by the body and two links
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int k = 0; k < ntraj; ++k)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], traj[9 * k + a]);
+      hi[a] = std::max(hi[a], traj[9 * k + a]);
+    }
+  const int dims[3] = {h->nx, h->ny, h->nz};
+  int o[3], e[3];
+  for (int a = 0; a < 3; ++a) {
+    if (a >= D) { o[a] = 0; e[a] = 1; continue; }
+    o[a] = (int)std::floor(lo[a] - ext[a] - 2.0);
+    const int hi_i = (int)std::ceil(hi[a] + ext[a] + 2.0);
+    e[a] = hi_i - o[a] + 1;
+    if (o[a] < 1 || hi_i > dims[a] - 2)
+      return lbm_fail(h, LBM_ERR_ARG, "the moving body's region must stay one node inside the lattice");
+  }
+  // static kinds in the region, widened by one node, must all be fluid
+  {
+    std::vector<uint8_t> fl(h->np);
+    LBM_CUDA_GEO(h, cudaMemcpyAsync(fl.data(), h->flags, h->np, cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA_GEO(h, cudaStreamSynchronize(h->stream));
+    for (int z = (D == 3 ? o[2] - 1 : 0); z < (D == 3 ? o[2] + e[2] + 1 : 1); ++z)
+      for (int y = o[1] - 1; y < o[1] + e[1] + 1; ++y)
+        for (int x = o[0] - 1; x < o[0] + e[0] + 1; ++x)
+          if ((fl[((long long)z * h->ny + y) * h->nxp + x] & 3) != K_FLUID)
+            return lbm_fail(h, LBM_ERR_ARG, "the moving body's region overlaps static solid or open nodes");
+  }
+  h->free_moving_body();
+  MovingBody &mb = h->mb;
+  mb.ox = o[0]; mb.oy = o[1]; mb.oz = o[2]; mb.rx = e[0]; mb.ry = e[1]; mb.rz = e[2];
+  mb.rsize = (long long)e[0] * e[1] * e[2];
+  mb.rpad = (mb.rsize + 31) / 32 * 32;
+  mb.ntraj = ntraj;
+  mb.cap_rec = mb.rsize;
+  mb.cap_link = mb.rsize * (h->Q - 1);
+  mb.tag = body->tag;
+  mb.nfpart = (mb.cap_rec + 255) / 256;
+  GeoShape gs;
+  std::memset(&gs, 0, sizeof(gs));
+  gs.type = body->type;
+  gs.tag = body->tag;
+  for (int a = 0; a < 3; ++a) gs.r[a] = body->r[a];
+  const size_t ls = h->link_size();
+  const long long nchunk = mb.rpad / 32;
+  LBM_CUDA_GEO(h, cudaMalloc(&mb.shape, sizeof(GeoShape)));
+  LBM_CUDA_GEO(h, cudaMalloc(&mb.traj, sizeof(double) * 9 * ntraj));
+  LBM_CUDA_GEO(h, cudaMalloc(&mb.step, sizeof(int)));
+  LBM_CUDA_GEO(h, cudaMalloc(&mb.fpart, sizeof(double) * 3 * mb.nfpart));
+  LBM_CUDA_GEO(h, cudaMemsetAsync(mb.fpart, 0, sizeof(double) * 3 * mb.nfpart, h->stream));
+  LBM_CUDA_GEO(h, cudaMalloc(&mb.crec, sizeof(uint32_t) * (nchunk + 1)));
+  LBM_CUDA_GEO(h, cudaMalloc(&mb.clink, sizeof(uint32_t) * (nchunk + 1)));
+  LBM_CUDA_GEO(h, cudaMalloc(&mb.tot, sizeof(uint32_t) * ((nchunk + 1023) / 1024 + 1)));
+  LBM_CUDA_GEO(h, cudaMalloc(&mb.totals, sizeof(uint32_t) * 2));
+  for (int k = 0; k < 2; ++k) {
+    LBM_CUDA_GEO(h, cudaMalloc(&mb.rec[k], sizeof(Rec) * mb.cap_rec));
+    LBM_CUDA_GEO(h, cudaMalloc(&mb.rnode[k], sizeof(uint32_t) * mb.cap_rec));
+    LBM_CUDA_GEO(h, cudaMalloc(&mb.lq[k], ls * mb.cap_link));
+    LBM_CUDA_GEO(h, cudaMalloc(&mb.luw[k], 3 * ls * mb.cap_link));
+    LBM_CUDA_GEO(h, cudaMalloc(&mb.luw1[k], 3 * ls * mb.cap_link));
+    LBM_CUDA_GEO(h, cudaMalloc(&mb.ltag[k], mb.cap_link));
+    LBM_CUDA_GEO(h, cudaMalloc(&mb.count[k], sizeof(int)));
+    LBM_CUDA_GEO(h, cudaMemsetAsync(mb.count[k], 0, sizeof(int), h->stream));
+  }
+  LBM_CUDA_GEO(h, cudaMemcpyAsync(mb.shape, &gs, sizeof(GeoShape), cudaMemcpyHostToDevice, h->stream));
+  LBM_CUDA_GEO(h, cudaMemcpyAsync(mb.traj, traj, sizeof(double) * 9 * ntraj, cudaMemcpyHostToDevice, h->stream));
+  LBM_CUDA_GEO(h, cudaMemcpyAsync(mb.step, &t0, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  mb.on = true;
+  ++h->version;
+  h->tiles_bx = h->tiles_by = 0;
+  h->drop_graphs();
+  // geometry of the pose t0 for the next step (no refill: the state is set afterwards
+  // or was set on the static geometry)
+  cudaError_t err = move_geometry(h, 0, 0, h->f[h->cur], h->cur);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
+  if (err != cudaSuccess) return lbm_fail(h, LBM_ERR_CUDA, std::string("moving body: ") + cudaGetErrorString(err));
+  // fluid node count of the current geometry
+  std::vector<uint8_t> fl(h->np);
+  LBM_CUDA_GEO(h, cudaMemcpy(fl.data(), h->flags, h->np, cudaMemcpyDeviceToHost));
+  long long nf = 0;
+  for (long long n = 0; n < h->np; ++n) nf += (fl[n] & 3) == K_FLUID;
+  h->nfluid = nf;
+  return LBM_OK;
 }

@@ -230,14 +230,14 @@ __device__ __forceinline__ int upstream_offset(const View &v, int x, int y, int 
 }
 
 template <class L, typename S, typename M>
-__device__ void boundary(const View &v, const Rec &r, const M *fs, int stride, const Macro<L, M> &m,
-                         long long n, int x, int y, int z, S *__restrict__ fout) {
-  const M *lq = static_cast<const M *>(v.lq);
-  const M *luw = static_cast<const M *>(v.luw);
-  const M *luw1 = static_cast<const M *>(v.luw1);
+__device__ void boundary(const View &v, const RecSet &rs, const Rec &r, const M *fs, int stride,
+                         const Macro<L, M> &m, long long n, int x, int y, int z, S *__restrict__ fout) {
+  const M *lq = static_cast<const M *>(rs.lq);
+  const M *luw = static_cast<const M *>(rs.luw);
+  const M *luw1 = static_cast<const M *>(rs.luw1);
   const Par<M> P(v);
   const uint32_t open = r.open & ~REC_MOVING;
-  const bool moving = v.has_uw && (r.open & REC_MOVING);
+  const bool moving = luw != nullptr && (r.open & REC_MOVING);
   uint32_t links = r.cut | open;
 #pragma unroll 1
   while (links) {
@@ -304,9 +304,9 @@ __device__ void boundary(const View &v, const Rec &r, const M *fs, int stride, c
 // BFL-completed), its moments, and the written-ahead unknowns of its wall and
 // open links. fs is this thread's column of the block's shared staging array.
 template <class L, typename S, typename M>
-__device__ __forceinline__ void boundary_node(const View &v, const Rec r, const S *__restrict__ fin,
-                                              S *__restrict__ fout, long long n, int x, int y, int z,
-                                              M *fs, int stride) {
+__device__ __forceinline__ void boundary_node(const View &v, const RecSet &rs, const Rec r,
+                                              const S *__restrict__ fin, S *__restrict__ fout, long long n,
+                                              int x, int y, int z, M *fs, int stride) {
   Nbr nb;
   nb.init(v, x, y, z);
   M f[L::Q];
@@ -315,7 +315,7 @@ __device__ __forceinline__ void boundary_node(const View &v, const Rec r, const 
   const Macro<L, M> m = moments<L, M>(v, f);
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) fs[i * stride] = f[i];
-  boundary<L, S, M>(v, r, fs, stride, m, n, x, y, z, fout);
+  boundary<L, S, M>(v, rs, r, fs, stride, m, n, x, y, z, fout);
 }
 
 // ---------------------------------------------------------------- the fused step
@@ -377,17 +377,27 @@ __device__ __forceinline__ void lattice_tile(const View &v, const S *__restrict_
   collide_store<L, S, M, FORCE>(v, f, m, fout + n, np);
 }
 
-// Boundary tile {-1 - count, first}: one thread per boundary record.
+// Boundary tile: one thread per boundary record. {-1 - count, first} takes static
+// records first .. first+count-1. {DYN_TILE, first} takes the moving body's
+// records first .. first+blocksize-1 that exist in this step (their number is
+// in device memory).
+constexpr int DYN_TILE = -(1 << 20);
 template <class L, typename S, typename M>
 __device__ __forceinline__ void boundary_tile(const View &v, const S *__restrict__ fin,
                                               S *__restrict__ fout, int2 tile, M *stage) {
   const int t = threadIdx.y * blockDim.x + threadIdx.x;
-  if (t >= -1 - tile.x) return;
+  const bool dyn = tile.x == DYN_TILE;
+  // signed arithmetic throughout: tiles past the moving body's record count get a
+  // negative count and do nothing
+  const int tpb = (int)(blockDim.x * blockDim.y);
+  const int count = dyn ? min(tpb, *v.dyn_count - tile.y) : -1 - tile.x;
+  if (t >= count) return;
+  const RecSet rs = dyn ? v.dyn : v.stat();
   const int rid = tile.y + t;
-  const Rec r = v.rec[rid];
-  const int n = (int)v.rnode[rid];
+  const Rec r = rs.rec[rid];
+  const int n = (int)rs.rnode[rid];
   const int x = n % v.nxp, y = (n / v.nxp) % v.ny, z = n / (v.nxp * v.ny);
-  boundary_node<L, S, M>(v, r, fin, fout, n, x, y, z, stage + t, 256);
+  boundary_node<L, S, M>(v, rs, r, fin, fout, n, x, y, z, stage + t, 256);
 }
 
 // Block b takes table entries b*T .. b*T+T-1 (T = v.tpb_tiles <= 4), whose
@@ -562,31 +572,33 @@ __global__ void __launch_bounds__(256) k_read(const View v, const S *__restrict_
 }
 
 // Momentum-exchange force (Sec. II.F, Eq. force-boundary-node) of the last step,
-// one thread per boundary record, links of one tag (tag < 0: all). It reads the
-// buffer just written: f*_ibar(x_F, t) from the node's own slot and
-// f_i(x_F, t+1) from the written-ahead slot (BFL-completed). Writes a per-block
-// FP64 partial (3 doubles).
+// one thread per boundary record of the set rs (nrec records, or *nrec_dev when
+// that is not null), links of one tag (tag < 0: all). It reads the buffer just
+// written: f*_ibar(x_F, t) from the node's own slot and f_i(x_F, t+1) from the
+// written-ahead slot (BFL-completed). Writes a per-block FP64 partial (3 doubles).
 template <class L, typename S, typename M>
-__global__ void __launch_bounds__(256) k_force(const View v, const S *__restrict__ cur, long long nb_,
-                                               int tag, double *__restrict__ part) {
+__global__ void __launch_bounds__(256) k_force(const View v, const S *__restrict__ cur, RecSet rs,
+                                               long long nrec, const int *nrec_dev, int tag,
+                                               double *__restrict__ part) {
   const long long rid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (nrec_dev) nrec = *nrec_dev;
   double fx = 0.0, fy = 0.0, fz = 0.0;
-  if (rid < nb_) {
-    const Rec r = v.rec[rid];
-    const long long n = v.rnode[rid];
+  if (rid < nrec) {
+    const Rec r = rs.rec[rid];
+    const long long n = rs.rnode[rid];
     const int x = (int)(n % v.nxp);
     const int y = (int)((n / v.nxp) % v.ny);
     const int z = (int)(n / ((long long)v.nxp * v.ny));
     Nbr nb;
     nb.init(v, x, y, z);
-    const M *lq = static_cast<const M *>(v.lq);
-    const M *luw = static_cast<const M *>(v.luw);
+    const M *lq = static_cast<const M *>(rs.lq);
+    const M *luw = static_cast<const M *>(rs.luw);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
       const uint32_t bit = 1u << i;
       if (!(r.cut & bit)) continue;
       const uint32_t li = r.link0 + __popc(r.cut & (bit - 1u));
-      if (tag >= 0 && v.ltag[li] != tag) continue;
+      if (tag >= 0 && rs.ltag[li] != tag) continue;
       const int ib = opp<L>(i);
       const double w = weight<L>(i);
       const double fpost_ib = (double)to_math<S, M>(cur[(long long)ib * v.np + n]) + w * v.rho0;
@@ -599,7 +611,7 @@ __global__ void __launch_bounds__(256) k_force(const View v, const S *__restrict
       }
       fnew += w * v.rho0;
       double wx = 0.0, wy = 0.0, wz = 0.0;
-      if (v.has_uw) { wx = (double)luw[3 * li]; wy = (double)luw[3 * li + 1]; wz = (double)luw[3 * li + 2]; }
+      if (luw) { wx = (double)luw[3 * li]; wy = (double)luw[3 * li + 1]; wz = (double)luw[3 * li + 2]; }
       fx += (-L::cx(i) - wx) * fpost_ib - (L::cx(i) - wx) * fnew;
       fy += (-L::cy(i) - wy) * fpost_ib - (L::cy(i) - wy) * fnew;
       fz += (-L::cz(i) - wz) * fpost_ib - (L::cz(i) - wz) * fnew;

@@ -112,6 +112,15 @@ struct Rec {
   uint32_t link0; // index of the first wall link of this node in the link arrays
 };
 
+// One set of boundary records and their per-link data (math type).
+struct RecSet {
+  const Rec *rec;         // [count] records, sorted by node (static) or region index (moving body)
+  const uint32_t *rnode;  // [count] padded node index of each record
+  const void *lq;         // [links] q of each wall link
+  const void *luw, *luw1; // [links*3] wall velocity at t, t+1, or null
+  const uint8_t *ltag;    // [links] force tag of each wall link
+};
+
 // Kernel view of one simulation (passed by value).
 struct View {
   int nx, ny, nz, nxp;       // extents; nxp = padded row length (multiple of 32)
@@ -132,6 +141,11 @@ struct View {
   const int2 *tiles;         // step-kernel block table (see k_step)
   int gx;                    // lattice tiles per row of tiles (nxp / block x)
   int ntiles, tpb_tiles;     // table length; consecutive table entries per block
+  // moving body: records of the nodes of its region, rebuilt every step
+  RecSet dyn;
+  const int *dyn_count;      // device: number of records in dyn (null: no moving body)
+
+  __host__ __device__ RecSet stat() const { return RecSet{rec, rnode, lq, luw, luw1, ltag}; }
   const void *lq;            // [nl] q of each wall link (math type)
   const void *luw, *luw1;    // [nl*3] wall velocity at t, t+1 (math type) or null
   const uint8_t *ltag;       // [nl] force tag of each wall link

@@ -24,8 +24,10 @@ cudaError_t launch_set_pop(int lattice, int dtype, const View &v, void *fout, co
                            const Launch &l);
 cudaError_t launch_read(int lattice, int dtype, const View &v, const void *fin, double *fh,
                         double *rho, double *u, double *mass_part, const Launch &l);
-cudaError_t launch_force(int lattice, int dtype, const View &v, const void *cur, long long nb,
-                         int tag, double *part, const Launch &l);
+// Momentum-exchange partials over the records rs: nrec of them, or *nrec_dev
+// (device) when nrec_dev is not null; the grid must cover the largest count.
+cudaError_t launch_force(int lattice, int dtype, const View &v, const void *cur, const RecSet &rs,
+                         long long nrec, const int *nrec_dev, int tag, double *part, const Launch &l);
 cudaError_t launch_reduce_final(const double *part, long long nblocks, int ncomp, double *out,
                                 cudaStream_t s);
 

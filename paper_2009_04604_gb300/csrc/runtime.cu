@@ -17,6 +17,7 @@
 #include "geometry.hpp"
 #include "launch.hpp"
 #include "sim.hpp"
+#include "kernels.cuh"
 
 using namespace lbm;
 
@@ -135,6 +136,7 @@ extern "C" int lbm_destroy(lbm_handle h) {
   h->free_geometry();
   cudaFree(h->f[0]); cudaFree(h->f[1]); cudaFree(h->flags); cudaFree(h->cbase);
   cudaFree(h->dres); cudaFree(h->scratch); cudaFree(h->tiles);
+  h->free_moving_body();
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
   return LBM_OK;
@@ -153,6 +155,8 @@ extern "C" int lbm_synchronize(lbm_handle h) {
 extern "C" int lbm_set_options(lbm_handle h, int bc, double rho0, const double force[3], int xshift) {
   if (!h) return lbm_fail(nullptr, LBM_ERR_ARG, "null handle");
   if (bc < LBM_BC_ELIBB_F || bc > LBM_BC_HWBB) return lbm_fail(h, LBM_ERR_ARG, "unknown boundary rule");
+  if (bc == LBM_BC_BFL && h->mb.on)
+    return lbm_fail(h, LBM_ERR_ARG, "BFL needs a second node along the link, which a moving body's records do not carry");
   if (!(rho0 > 0.0) || !std::isfinite(rho0)) return lbm_fail(h, LBM_ERR_ARG, "rho0 must be positive");
   if (h->geom_ok && h->state_ok && rho0 != h->rho0)
     return lbm_fail(h, LBM_ERR_STATE, "rho0 changes the stored shift: set it before the state");
@@ -197,6 +201,13 @@ View lbm_sim::view() const {
   v.flags = flags; v.cbase = cbase; v.rec = rec; v.rnode = rnode; v.nb = nb;
   v.tiles = tiles; v.gx = nxp / step_bx;
   v.ntiles = (int)ntiles; v.tpb_tiles = tiles_per_block;
+  if (mb.on) {
+    v.dyn = RecSet{mb.rec[cur], mb.rnode[cur], mb.lq[cur], mb.luw[cur], mb.luw1[cur], mb.ltag[cur]};
+    v.dyn_count = mb.count[cur];
+  } else {
+    v.dyn = RecSet{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    v.dyn_count = nullptr;
+  }
   v.lq = lq; v.luw = luw; v.luw1 = luw1; v.ltag = ltag;
   return v;
 }
@@ -246,6 +257,8 @@ int lbm_sim::ensure_tiles() {
     const long long r0 = hc[z * pchunks], r1 = hc[(z + 1) * pchunks];
     for (long long r = r0; r < r1; r += tpb) t.push_back(make_int2(-1 - (int)std::min<long long>(tpb, r1 - r), (int)r));
   }
+  if (mb.on)  // the moving body's records: as many tiles as the region could need
+    for (long long r = 0; r < mb.cap_rec; r += tpb) t.push_back(make_int2(DYN_TILE, (int)r));
   cudaFree(tiles);
   tiles = nullptr;
   ntiles = (long long)t.size();
@@ -339,17 +352,30 @@ extern "C" int lbm_wall_force(lbm_handle h, int tag, double F[3]) {
   if (!h->geom_ok || !h->state_ok) return lbm_fail(h, LBM_ERR_STATE, "no state yet");
   if (tag < -1 || tag > 7) return lbm_fail(h, LBM_ERR_ARG, "tag must be -1..7");
   F[0] = F[1] = F[2] = 0.0;
-  if (h->nb == 0) return LBM_OK;
   const int bs = 256;
-  const long long nblk = (h->nb + bs - 1) / bs;
-  int rc = h->ensure_scratch(nblk * 3);
+  const long long nblk1 = (h->nb + bs - 1) / bs;
+  const long long nblk2 = h->mb.on ? h->mb.nfpart : 0;
+  if (nblk1 + nblk2 == 0) return LBM_OK;
+  int rc = h->ensure_scratch((nblk1 + nblk2) * 3);
   if (rc) return rc;
   Launch l;
-  l.grid = dim3((unsigned)nblk);
   l.block = dim3(bs);
   l.stream = h->stream;
-  LBM_CUDA(h, launch_force(h->lattice, h->dtype, h->view(), h->f[h->cur], h->nb, tag, h->scratch, l));
-  LBM_CUDA(h, launch_reduce_final(h->scratch, nblk, 3, h->dres, h->stream));
+  const View v = h->view();
+  if (nblk1) {
+    l.grid = dim3((unsigned)nblk1);
+    LBM_CUDA(h, launch_force(h->lattice, h->dtype, v, h->f[h->cur], v.stat(), h->nb, nullptr, tag,
+                             h->scratch, l));
+  }
+  if (nblk2) {
+    // the moving body's partials, taken during the last step before its refill
+    if (tag < 0 || tag == h->mb.tag)
+      LBM_CUDA(h, cudaMemcpyAsync(h->scratch + nblk1 * 3, h->mb.fpart, nblk2 * 3 * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, h->stream));
+    else
+      LBM_CUDA(h, cudaMemsetAsync(h->scratch + nblk1 * 3, 0, nblk2 * 3 * sizeof(double), h->stream));
+  }
+  LBM_CUDA(h, launch_reduce_final(h->scratch, nblk1 + nblk2, 3, h->dres, h->stream));
   LBM_CUDA(h, cudaMemcpyAsync(F, h->dres, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   LBM_CUDA(h, cudaStreamSynchronize(h->stream));
   return LBM_OK;
@@ -372,6 +398,10 @@ int lbm_sim::launch_steps(int n) {
   for (int k = 0; k < n; ++k) {
     cudaError_t e = launch_step(lattice, dtype, variant, view(), f[cur], f[cur ^ 1], step_shape());
     if (e != cudaSuccess) return lbm_fail(this, LBM_ERR_CUDA, cudaGetErrorString(e));
+    if (mb.on) {
+      int rc = move_after_step(f[cur ^ 1], cur ^ 1);
+      if (rc) return rc;
+    }
     cur ^= 1;
   }
   return LBM_OK;
@@ -427,6 +457,7 @@ extern "C" int lbm_set_geometry(lbm_handle h, const uint8_t *flags, const double
 
 int lbm_sim::upload(const HostGeometry &g) {
   ++version;
+  free_moving_body();
   drop_graphs();
   free_geometry();
   tiles_bx = tiles_by = 0;

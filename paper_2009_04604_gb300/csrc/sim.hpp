@@ -12,6 +12,30 @@ namespace lbm {
 struct HostGeometry;
 }
 
+// A rigid body moving along a prescribed trajectory. Its link geometry is
+// rebuilt on the device after every step, inside a fixed region box that covers
+// the whole trajectory. The records are double-buffered by the population
+// buffer index: set k serves the step that reads buffer k.
+struct MovingBody {
+  bool on = false;
+  void *shape = nullptr;           // device copy of the body's shape (geometry kernels' type)
+  double *traj = nullptr;          // device [ntraj][9]: centre, velocity, angular velocity per step
+  int ntraj = 0;
+  int ox = 0, oy = 0, oz = 0, rx = 1, ry = 1, rz = 1;  // region box
+  long long rsize = 0, rpad = 0;   // region nodes; rounded up to 32
+  lbm::Rec *rec[2] = {nullptr, nullptr};
+  uint32_t *rnode[2] = {nullptr, nullptr};
+  void *lq[2] = {nullptr, nullptr}, *luw[2] = {nullptr, nullptr}, *luw1[2] = {nullptr, nullptr};
+  uint8_t *ltag[2] = {nullptr, nullptr};
+  int *count[2] = {nullptr, nullptr};  // device: records in each set
+  uint32_t *crec = nullptr, *clink = nullptr, *tot = nullptr, *totals = nullptr;  // scan scratch
+  int *step = nullptr;             // device: index of the body's current pose
+  long long cap_rec = 0, cap_link = 0;
+  int tag = 0;
+  double *fpart = nullptr;         // device: per-block momentum-exchange partials of the last step
+  long long nfpart = 0;            // blocks
+};
+
 struct lbm_sim {
   static constexpr int kGraphSteps = 32;  // steps per captured CUDA graph (even)
 
@@ -49,6 +73,7 @@ struct lbm_sim {
   int step_bx = 32, step_by = 8, variant = 0;
   bool geom_ok = false, state_ok = false;
   int version = 0;  // bumped whenever the kernel view changes (options, geometry)
+  MovingBody mb;
   std::string err;
 
   size_t elem_size() const;
@@ -65,6 +90,8 @@ struct lbm_sim {
   void drop_graphs();
   int launch_steps(int n);
   int ensure_tiles();
+  int move_after_step(void *fout, int set);  // body geometry for the next step (geometry.cu)
+  void free_moving_body();
   int capture(int parity);
   int upload(const lbm::HostGeometry &g);
   int download(lbm::HostGeometry &g);

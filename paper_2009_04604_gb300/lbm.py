@@ -69,6 +69,7 @@ _SIGS = {
     "lbm_get_launch": [ctypes.c_void_p, _int, _int, _int, _int],
     "lbm_autotune": [ctypes.c_void_p, ctypes.c_int, _int, _int, _int, _int, _d],
     "lbm_mass_noalloc": [ctypes.c_void_p, ctypes.c_void_p],
+    "lbm_set_moving_body": [ctypes.c_void_p, P(Shape), _d, ctypes.c_int, ctypes.c_int],
     "lbm_batch_create": [P(ctypes.c_void_p), ctypes.c_int, P(ctypes.c_void_p)],
     "lbm_batch_destroy": [ctypes.c_void_p],
     "lbm_batch_step": [ctypes.c_void_p, ctypes.c_int],
@@ -204,6 +205,12 @@ class Simulation:
         arr = make_shapes(list(shapes))
         self._ok(self.lib.lbm_build_geometry(self.h, _np_ptr(base, ctypes.c_uint8),
                                              _np_ptr(base_u, ctypes.c_double), arr, len(shapes)))
+
+    def set_moving_body(self, body, traj, t0=0):
+        """Rigid body (dict spec: sphere or ellipsoid) on the trajectory traj[k] = (c[3], v[3], om[3])."""
+        traj = _f64(traj, (-1, 9))
+        arr = make_shapes([body])
+        self._ok(self.lib.lbm_set_moving_body(self.h, arr, _np_ptr(traj, ctypes.c_double), traj.shape[0], int(t0)))
 
     def init(self, rho=1.0, u=(0.0, 0.0, 0.0)):
         U = (ctypes.c_double * 3)(*[float(x) for x in u])
