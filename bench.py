@@ -223,6 +223,34 @@ def dtype_variant(torch, lbm, W, dtype, steps, peak):
             "roofline_frac": round(ach / peak, 4), "achieved_gbs": round(ach, 1), "launch": tuned}
 
 
+def porous_moving(torch, lbm, W, dtype, steps, peak):
+    """Porous-medium configuration at full size: 384^3 periodic box of static
+    spheres plus one sphere on a sinusoidal path whose link geometry is rebuilt on
+    the device every step; body force 1e-6."""
+    if "wl" not in porous_cache:
+        porous_cache["wl"] = W.porous_with_moving_sphere()
+    wl = porous_cache["wl"]
+    s = lbm.Simulation(wl["lattice"], wl["dims"], wl["tau"], dtype)
+    s.set_options("elibb_f", wl["rho0"], wl["force"], 0)
+    s.build_geometry(None, None, wl["shapes"])
+    s.set_moving_body(wl["body"], wl["traj"], 0)
+    s.init(wl["rho0"])
+    tuned = s.autotune(4)
+    s.step(4)
+    ms = time_steps(torch, s.stream, s.step, steps)
+    nfluid, nb, nl = s.counts()
+    _, u = s.macros()
+    finite = bool(torch.isfinite(u).all().item())
+    s.close()
+    return {"value": round(nfluid * steps / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "dtype": dtype,
+            "steps": steps, "nfluid": nfluid, "static_boundary_nodes": nb, "static_wall_links": nl,
+            "porosity": round(wl["porosity"], 4), "static_shapes": len(wl["shapes"]), "finite": finite,
+            "ms_per_step": round(ms / steps, 4), "launch": tuned}
+
+
+porous_cache = {}
+
+
 def batched_vs_plain(torch, lbm, W, regime, dtype, steps):
     """Batched configuration: many D3Q19 ducts, one launch per step for all (graph
     replay) against one launch per simulation per step. The per-node code is the
@@ -381,6 +409,11 @@ def ours_arm(args, rank, world, dist):
                     extras[dt] = dtype_variant(torch, lbm, W, dt, min(args.steps, 400), peak)
                 except Exception as exc:
                     extras[dt] = {"error": str(exc)[:200]}
+        for dt in ("f32", "f16"):
+            try:
+                extras["porous_moving_" + dt] = porous_moving(torch, lbm, W, dt, 100, peak)
+            except Exception as exc:
+                extras["porous_moving_" + dt] = {"error": str(exc)[:200]}
         for regime, st_ in (("large", 100), ("small", 400)):
             try:
                 extras["batched_" + regime] = batched_vs_plain(torch, lbm, W, regime, "f32", st_)

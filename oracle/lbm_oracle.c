@@ -454,6 +454,7 @@ long or_geometry(const or_params *p, const uint8_t *base, const double *base_u,
   const int Q = L.Q, D = L.D;
   const int nx = p->nx, ny = p->ny, nz = p->nz;
   const long N = (long)nx * ny * nz;
+#pragma omp parallel for schedule(static)
   for (long n = 0; n < N; ++n) {
     int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long)nx * ny));
     double X[3] = {(double)x, (double)y, (double)z};
@@ -464,6 +465,7 @@ long or_geometry(const or_params *p, const uint8_t *base, const double *base_u,
     flags[n] = fl;
   }
   long ncut = 0;
+#pragma omp parallel for schedule(static) reduction(+ : ncut)
   for (long n = 0; n < N; ++n) {
     int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long)nx * ny));
     double X[3] = {(double)x, (double)y, (double)z};

@@ -87,14 +87,18 @@ def porous_spheres(n=384, porosity=0.6, rmin=6.0, rmax=12.0, seed=7, moving_radi
                    amplitude=20.0, clearance=4.0, max_attempts=200000):
     """Periodic box of non-overlapping spheres placed largest first by random
     sequential addition (radii uniform in [rmin, rmax]) towards the target
-    porosity, keeping a tube around the moving sphere's path free. Spheres that
-    cross the periodic boundary are listed once per periodic image. Returns
-    (static shape list, achieved porosity estimate, path centre)."""
+    porosity. The box around the moving sphere's path (its extent along x plus
+    moving_radius + clearance on every side) is kept free. Spheres that cross the
+    periodic boundary are listed once per periodic image. Random sequential
+    addition jams near a solid fraction of 0.4, so the attempt budget may stop
+    short of the target. Returns (static shape list, achieved porosity, path
+    centre)."""
     rng = np.random.default_rng(seed)
     L = float(n)
     target_solid = (1.0 - porosity) * L ** 3
     c0 = np.array([L / 2, L / 2, L / 2])
-    tube_r = moving_radius + clearance
+    half = np.array([amplitude + moving_radius + clearance, moving_radius + clearance,
+                     moving_radius + clearance])
     mean_vol = 4.0 / 3.0 * math.pi * (rmax ** 4 - rmin ** 4) / (4 * (rmax - rmin))
     nwant = int(target_solid / mean_vol * 1.2) + 16
     radii = np.sort(rng.uniform(rmin, rmax, nwant))[::-1]
@@ -110,9 +114,9 @@ def porous_spheres(n=384, porosity=0.6, rmin=6.0, rmax=12.0, seed=7, moving_radi
         for _ in range(200):
             attempts += 1
             p = rng.uniform(0, L, 3)
-            # tube around the moving sphere's path (x from c0-amp to c0+amp)
-            dx = max(0.0, abs(p[0] - c0[0]) - amplitude)
-            if math.hypot(math.hypot(dx, p[1] - c0[1]), p[2] - c0[2]) < tube_r + r:
+            # keep the box around the moving sphere's path free
+            gap = np.maximum(np.abs(p - c0) - half, 0.0)
+            if gap @ gap < r * r:
                 continue
             ci = tuple(int(v // cell) % nc for v in p)
             ok = True
@@ -234,3 +238,23 @@ def batched_ducts(n=96, lo=48, hi=192, target=1.2e8, tol=0.05, seed=11, rmin=6.0
         out.append(dict(lattice=D3Q19, dims=d, tau=tau, xshift=0, force=(0.0, 0.0, 0.0), base=base,
                         base_u=base_u, shapes=[shape], rho0=1.0, u_in=u_in))
     return out
+
+
+def porous_with_moving_sphere(n=384, seed=7, rmin=6.0, rmax=12.0, moving_radius=10.0, amplitude=20.0,
+                              period=5000, tau=0.65, g=1e-6, porosity=0.6, max_attempts=200000):
+    """The porous-medium configuration: D3Q19, periodic n^3 box of static spheres,
+    one sphere of radius moving_radius moving on c(t) = c0 + A sin(2 pi t / T) e_x,
+    and a body force g along x. The trajectory table holds one period of poses
+    (centre, velocity = path derivative, zero angular velocity)."""
+    shapes, por, c0 = porous_spheres(n, porosity, rmin, rmax, seed, moving_radius, amplitude,
+                                     max_attempts=max_attempts)
+    w = 2.0 * math.pi / period
+    t = np.arange(period)
+    traj = np.zeros((period, 9))
+    traj[:, 0] = c0[0] + amplitude * np.sin(w * t)
+    traj[:, 1] = c0[1]
+    traj[:, 2] = c0[2]
+    traj[:, 3] = amplitude * w * np.cos(w * t)
+    body = dict(type="sphere", tag=1, r=(moving_radius, 0, 0))
+    return dict(lattice=D3Q19, dims=(n, n, n), tau=tau, xshift=0, force=(g, 0.0, 0.0), base=None,
+                base_u=None, shapes=shapes, rho0=1.0, body=body, traj=traj, porosity=por)

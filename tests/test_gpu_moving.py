@@ -108,3 +108,38 @@ def test_moving_body_f32_runs_and_rejects_bad_regions():
     with pytest.raises(lbm.LBMError):
         s.set_moving_body(body, traj, 0)
     s.close()
+
+
+@pytest.mark.parametrize("dtype,bound", [(lbm.F64, 1e-12), (lbm.F32, 1e-5), (lbm.F16, 1e-3)])
+def test_porous_moving_sphere_downscale(dtype, bound):
+    """Porous medium with a moving sphere (downscale of the 384^3 configuration):
+    static spheres from random sequential addition, a sphere on a sinusoidal path,
+    body force; velocity against the FP64 oracle."""
+    from paper_2009_04604_gb300 import workloads as W
+    wl = W.porous_with_moving_sphere(n=48, rmin=3.0, rmax=5.0, moving_radius=4.0, amplitude=3.0,
+                                     period=300, seed=5, g=1e-5)
+    steps = 20
+    traj, body = wl["traj"], wl["body"]
+    p = oracle.params(lbm.D3Q19, wl["dims"], wl["tau"], bc=oracle.BC_ELIBB_F, force=wl["force"])
+    stat = oracle_shapes(wl["shapes"])
+    flags, *_ = oracle.geometry(p, None, None, stat + oracle_shapes([moving_shape(body, traj, 0)]))
+    f = oracle.init_eq(p, flags)
+    for t in range(steps):
+        fl_t, q, uw, uw1, tag = oracle.geometry(p, None, None, stat + oracle_shapes([moving_shape(body, traj, t)]))
+        f = oracle.step(p, fl_t, f, q, uw, uw1)
+        fl_n, *_ = oracle.geometry(p, None, None, stat + oracle_shapes([moving_shape(body, traj, t + 1)]))
+        oracle.refill(p, fl_t, fl_n, np.tile(traj[(t + 1) % len(traj), 3:6], (fl_n.size, 1)), f)
+        flags = fl_n
+    _, uo = oracle.macros(p, flags, f)
+    s = lbm.Simulation(lbm.D3Q19, wl["dims"], wl["tau"], dtype)
+    s.set_options(lbm.BC_ELIBB_F, 1.0, wl["force"], 0)
+    s.build_geometry(None, None, wl["shapes"])
+    s.set_moving_body(body, traj, 0)
+    s.init(1.0)
+    s.step(steps)
+    assert np.array_equal(s.get_geometry()[0], flags)
+    _, u = s.macros()
+    fl = flags == 0
+    err = rel_l2(u.cpu().numpy()[fl], uo[fl])
+    assert err < bound, err
+    s.close()

@@ -279,3 +279,41 @@ def test_edge_cases():
     with pytest.raises(lbm.LBMError):
         s.step(1)  # no geometry yet
     s.close()
+
+
+def test_nonfinite_state_is_reported():
+    """A NaN planted in a host copy of the state is found by the FP64 mass reduction
+    and reported as LBM_ERR_NONFINITE; the context stays usable."""
+    wl = W.sphere_duct_small()
+    s = gpu_sim(wl, lbm.F32)
+    s.build_geometry(wl["base"], wl["base_u"], wl["shapes"])
+    s.init(1.0)
+    s.step(3)
+    f = s.get_populations()
+    fl = s.get_geometry()[0] == 0
+    f[np.nonzero(fl)[0][100], 7] = np.nan
+    s.set_populations(f)
+    with pytest.raises(lbm.LBMError) as e:
+        s.mass()
+    assert e.value.code == -4
+    s.init(1.0)  # recover by re-initialising
+    assert np.isfinite(s.mass())
+    s.close()
+
+
+def test_full_size_step_conserves_mass_in_closed_box():
+    """Full-size launch shape of the benchmark (256 x 128 x 128, autotuned), closed box
+    with static walls and a sphere: half-way walls at rest conserve mass exactly up
+    to rounding, a property that holds at any size."""
+    wl = W.sphere_duct()
+    base = wl["base"].copy()
+    base[base == 2] = 1                      # close the outlet
+    s = gpu_sim(wl, lbm.F64, lbm.BC_HWBB)
+    s.build_geometry(base, None, wl["shapes"])
+    s.init(1.0, (0.01, 0.0, 0.0))
+    m0 = s.mass()
+    s.autotune(2)
+    s.step(64)
+    m1 = s.mass()
+    assert abs(m1 - m0) / m0 < 1e-12, (m0, m1)
+    s.close()
