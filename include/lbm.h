@@ -213,7 +213,11 @@ int lbm_get_counts(lbm_handle h, int64_t *n_fluid, int64_t *n_boundary, int64_t 
  *   bx x by threads per block: bx a multiple of 32 that divides the padded row
  *     length, bx*by <= 256;
  *   variant 0..3: the register budget. Variant v guarantees v+1 resident
- *     256-thread blocks per SM. FP64 storage accepts variant 0 only;
+ *     256-thread blocks per SM;
+ *   variant 4: the TMA-staged persistent kernel. One thread per block copies
+ *     each lattice tile's source rows into shared memory with bulk asynchronous
+ *     copies, several tiles ahead, and the block computes from there. FP32,
+ *     FP16 and BF16 only. FP64 storage accepts variant 0 only;
  *   tiles 1..4: consecutive entries of the step kernel's tile table that one
  *     block processes. The table lists, plane by plane, the lattice tiles and
  *     then the boundary-record tiles.

@@ -420,6 +420,199 @@ __global__ void __launch_bounds__(256, MINB) k_step(const View v, const S *__res
   }
 }
 
+// ---------------------------------------------------------------- TMA-staged step
+// A persistent variant of k_step for FP32/FP16/BF16 storage. Each block walks
+// the tile table with a grid stride. For a lattice tile, one producer thread
+// copies every source row the tile needs into a shared-memory stage with bulk
+// asynchronous copies (cp.async.bulk, completion counted on an mbarrier):
+//  - for each population plane i and tile row h, the row y0 + h - c_iy of plane
+//    z - c_iz (rows wrap in y and z), over x0 - HALO .. x0 + W + HALO, where
+//    HALO is one 16-byte chunk, clipped to the padded row;
+//  - the tile's flag rows.
+// The producer runs nstage - 1 entries ahead (nstage <= 16: the stage parities
+// are kept in one word), so the loads in flight are bounded by shared memory, not
+// by registers. Consumers read f_i(x) = stage[i][row][x - c_ix]
+// and take a direct (wrapped) load only when x - c_ix leaves [0, nx). Boundary
+// tiles run as in k_step, staging in the entry's shared slot. Every mbarrier
+// wait is bounded: if it runs out, the block sets bit 0 of *v.err, waits (again
+// bounded) for its copies in flight, and leaves.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+constexpr long long kWaitLimit = 1LL << 24;  // try_wait polls before a wait counts as hung
+
+// Bounded wait on one mbarrier phase. Returns false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+  for (long long k = 0; k < kWaitLimit; ++k)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+template <typename S>
+struct TmaLayout {
+  static constexpr int HALO = 16 / (int)sizeof(S);  // elements in one 16-byte chunk
+  int W, H, rowlen;                                 // rowlen = W + 2 HALO
+  __device__ __forceinline__ TmaLayout(int w, int h) : W(w), H(h), rowlen(w + 2 * HALO) {}
+  template <class L>
+  __device__ __forceinline__ int pops_bytes() const { return L::Q * H * rowlen * (int)sizeof(S); }
+};
+
+// Producer: copies of lattice tile `tile` into stage buffer `base`, armed on `bar`.
+// Called by all 32 lanes of warp 0: lane 0 arms the barrier with the byte count,
+// then the lanes share the row copies (rows of the Q planes, then the flag rows).
+template <class L, typename S>
+__device__ void tma_issue(const View &v, const S *__restrict__ fin, int2 tile, unsigned char *base,
+                          uint64_t *bar, const TmaLayout<S> &lay, int lane) {
+  constexpr int HALO = TmaLayout<S>::HALO;
+  const int W = lay.W, H = lay.H;
+  const int z = tile.x, x0 = (tile.y % v.gx) * W, y0 = (tile.y / v.gx) * H;
+  const int xa = max(x0 - HALO, 0), xb = min(x0 + W + HALO, v.nxp);
+  const int rows = min(H, v.ny - y0);
+  const uint32_t rowbytes = (uint32_t)((xb - xa) * (int)sizeof(S));
+  if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)L::Q * rows * rowbytes + (uint32_t)rows * W);
+  __syncwarp();
+  S *pops = reinterpret_cast<S *>(base);
+  unsigned char *fl = base + lay.template pops_bytes<L>();
+  const long long plane = (long long)v.nxp * v.ny;
+  const int ncopy = (L::Q + 1) * rows;
+  for (int c = lane; c < ncopy; c += 32) {
+    const int i = c / rows, h = c - i * rows;
+    if (i == L::Q) {
+      bulk_g2s(fl + h * W, v.flags + (z * (long long)v.ny + y0 + h) * v.nxp + x0, (uint32_t)W, bar);
+    } else {
+      int zs = z - dcz<L>(i);
+      zs = zs < 0 ? zs + v.nz : (zs >= v.nz ? zs - v.nz : zs);
+      int ys = y0 + h - dcy<L>(i);
+      ys = ys < 0 ? ys + v.ny : (ys >= v.ny ? ys - v.ny : ys);
+      const S *src = fin + (long long)i * v.np + zs * plane + (long long)ys * v.nxp + xa;
+      S *dst = pops + ((long long)i * H + h) * lay.rowlen + (xa - (x0 - HALO));
+      bulk_g2s(dst, src, rowbytes, bar);
+    }
+  }
+}
+
+// Consumer: one node per thread from the stage.
+template <class L, typename S, typename M, bool FORCE>
+__device__ __forceinline__ void tma_lattice(const View &v, const S *__restrict__ fin, S *__restrict__ fout,
+                                            int2 tile, const unsigned char *base, const TmaLayout<S> &lay) {
+  constexpr int HALO = TmaLayout<S>::HALO;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x = (tile.y % v.gx) * lay.W + tx;
+  const int y = (tile.y / v.gx) * lay.H + ty;
+  const int z = tile.x;
+  if (y >= v.ny) return;  // uniform across the warp
+  const int n = (z * v.ny + y) * v.nxp + x;
+  const uint8_t fl = base[lay.template pops_bytes<L>() + ty * lay.W + tx];
+  uint32_t bal = 0;
+  if (v.bc == BC_BFL) bal = __ballot_sync(0xffffffffu, fl & F_BOUNDARY);
+  if ((fl & 3) != K_FLUID) return;
+  const S *pops = reinterpret_cast<const S *>(base);
+  const bool xedge = x == 0 || x >= v.nx - 1;
+  const int np = (int)v.np;
+  M f[L::Q];
+  if (!xedge) {
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+      f[i] = to_math<S, M>(pops[(i * lay.H + ty) * lay.rowlen + tx + HALO - L::cx(i)]);
+  } else {
+    Nbr nb;
+    nb.init(v, x, y, z);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+      f[i] = L::cx(i) == 0 ? to_math<S, M>(pops[(i * lay.H + ty) * lay.rowlen + tx + HALO])
+                           : to_math<S, M>(__ldg(fin + (long long)i * v.np + n +
+                                                 nb.at(-L::cx(i), -L::cy(i), -L::cz(i))));
+  }
+  if (v.bc == BC_BFL && (fl & F_BOUNDARY)) bfl_complete<L, M>(v, *record_of(v, n, bal), f);
+  const Macro<L, M> m = moments<L, M>(v, f);
+  collide_store<L, S, M, FORCE>(v, f, m, fout + n, np);
+}
+
+template <class L, typename S, typename M, bool FORCE>
+__global__ void __launch_bounds__(256, 2) k_step_tma(const View v, const S *__restrict__ fin,
+                                                     S *__restrict__ fout, int nstage, int stage_bytes) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+  unsigned char *stages = smem + 128;
+  const TmaLayout<S> lay(blockDim.x, blockDim.y);
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  const int G = gridDim.x;
+  if (t == 0) {
+    for (int k = 0; k < nstage; ++k) mbar_init(&bars[k], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (t < 32)
+    for (int j = 0; j < nstage - 1; ++j) {
+      const int e = blockIdx.x + j * G;
+      if (e >= v.ntiles) break;
+      const int2 tl = v.tiles[e];
+      if (tl.x >= 0) tma_issue<L, S>(v, fin, tl, stages + j * stage_bytes, &bars[j], lay, t);
+    }
+  uint32_t parity = 0;  // bit k: parity of the next wait on stage k
+  for (int j = 0;; ++j) {
+    const int e = blockIdx.x + j * G;
+    if (e >= v.ntiles) break;  // uniform across the block
+    const int k = j % nstage;
+    if (t < 32) {
+      const int en = e + (nstage - 1) * G;
+      const int kn = (j + nstage - 1) % nstage;
+      if (en < v.ntiles) {
+        const int2 tl = v.tiles[en];
+        if (tl.x >= 0) {
+          fence_proxy_async_smem();  // order earlier generic accesses of the stage before the copies
+          tma_issue<L, S>(v, fin, tl, stages + kn * stage_bytes, &bars[kn], lay, t);
+        }
+      }
+    }
+    const int2 tile = v.tiles[e];
+    if (tile.x < 0) {
+      boundary_tile<L, S, M>(v, fin, fout, tile, reinterpret_cast<M *>(stages + k * stage_bytes));
+    } else {
+      const bool ok = mbar_wait_bounded(&bars[k], (parity >> k) & 1u);
+      if (__syncthreads_or(!ok)) {  // the whole block leaves together
+        if (t == 0) {
+          atomicOr(v.err, 1);
+          for (int q = 0; q < nstage; ++q) mbar_wait_bounded(&bars[q], (parity >> q) & 1u);
+        }
+        return;
+      }
+      parity ^= 1u << k;
+      tma_lattice<L, S, M, FORCE>(v, fin, fout, tile, stages + k * stage_bytes, lay);
+    }
+    __syncthreads();  // the stage is free for the producer
+  }
+}
+
 // ---------------------------------------------------------------- batched step
 // Many independent simulations advance in one launch. Entry k holds the view
 // and the two population buffers of simulation k. The tile table lists

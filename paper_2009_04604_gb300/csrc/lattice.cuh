@@ -144,6 +144,7 @@ struct View {
   // moving body: records of the nodes of its region, rebuilt every step
   RecSet dyn;
   const int *dyn_count;      // device: number of records in dyn (null: no moving body)
+  int *err;                  // device error word (bounded waits that ran out set bit 0)
 
   __host__ __device__ RecSet stat() const { return RecSet{rec, rnode, lq, luw, luw1, ltag}; }
   const void *lq;            // [nl] q of each wall link (math type)

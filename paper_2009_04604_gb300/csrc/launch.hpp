@@ -11,11 +11,19 @@ namespace lbm {
 struct Launch {
   dim3 grid, block;
   cudaStream_t stream;
+  int smem = 0;  // dynamic shared memory (TMA-staged step)
 };
+
+// Sets the shared-memory limit of the TMA-staged step kernel for this launch shape
+// and returns its persistent grid (SMs x resident blocks, at most ntiles) and its
+// dynamic shared memory. Call outside stream capture.
+cudaError_t prepare_step_tma(int lattice, int dtype, int has_force, int bx, int by, long long ntiles,
+                             int *blocks, int *smem);
 
 // lattice: 0 D2Q9, 1 D3Q19; dtype: 0 F64, 1 F32, 2 F16, 3 BF16
 // variant: register budget of the step kernel, at least variant+1 resident
-// 256-thread blocks per SM (0..3); FP64 has a single variant.
+// 256-thread blocks per SM (0..3), or 4: the TMA-staged persistent kernel
+// (FP32/FP16/BF16). FP64 has a single variant.
 cudaError_t launch_step(int lattice, int dtype, int variant, const View &v, const void *fin,
                         void *fout, const Launch &l);
 cudaError_t launch_init(int lattice, int dtype, const View &v, void *fout, double rho, double ux,

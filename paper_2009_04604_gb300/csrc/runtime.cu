@@ -103,6 +103,8 @@ extern "C" int lbm_create(int lattice, const int dims[3], double tau, int dtype,
   if (e == cudaSuccess) e = cudaMalloc(&h->flags, np);
   if (e == cudaSuccess) e = cudaMalloc(&h->cbase, (np / 32 + 1) * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&h->dres, 8 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&h->err_dev, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->flags, K_PAD, np, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->f[0], 0, bytes, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->f[1], 0, bytes, h->stream);
@@ -135,7 +137,7 @@ extern "C" int lbm_destroy(lbm_handle h) {
   h->drop_graphs();
   h->free_geometry();
   cudaFree(h->f[0]); cudaFree(h->f[1]); cudaFree(h->flags); cudaFree(h->cbase);
-  cudaFree(h->dres); cudaFree(h->scratch); cudaFree(h->tiles);
+  cudaFree(h->dres); cudaFree(h->scratch); cudaFree(h->tiles); cudaFree(h->err_dev);
   h->free_moving_body();
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -149,6 +151,12 @@ extern "C" const char *lbm_last_error(lbm_handle h) {
 extern "C" int lbm_synchronize(lbm_handle h) {
   if (!h) return lbm_fail(nullptr, LBM_ERR_ARG, "null handle");
   LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  int err = 0;
+  LBM_CUDA(h, cudaMemcpy(&err, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    cudaMemset(h->err_dev, 0, sizeof(int));
+    return lbm_fail(h, LBM_ERR_TIMEOUT, "a bounded wait in the step kernel ran out; the step is incomplete");
+  }
   return LBM_OK;
 }
 
@@ -184,6 +192,7 @@ extern "C" int lbm_set_options(lbm_handle h, int bc, double rho0, const double f
   if (h->lattice == LBM_D2Q9) { h->F[2] = 0.0; }
   h->xshift = xshift;
   h->drop_graphs();
+  h->tiles_var = -1;  // the TMA-staged step is prepared per force path
   ++h->version;
   return LBM_OK;
 }
@@ -199,6 +208,7 @@ View lbm_sim::view() const {
   v.omega_f = (float)v.omega; v.rho0_f = (float)rho0; v.qcut_f = (float)qcut;
   for (int a = 0; a < 3; ++a) v.F_f[a] = (float)F[a];
   v.flags = flags; v.cbase = cbase; v.rec = rec; v.rnode = rnode; v.nb = nb;
+  v.err = err_dev;
   v.tiles = tiles; v.gx = nxp / step_bx;
   v.ntiles = (int)ntiles; v.tpb_tiles = tiles_per_block;
   if (mb.on) {
@@ -234,6 +244,10 @@ Launch lbm_sim::step_shape() const {
   l.block = dim3(step_bx, step_by, 1);
   l.grid = dim3((unsigned)((ntiles + tiles_per_block - 1) / tiles_per_block), 1, 1);
   l.stream = stream;
+  if (variant == 4) {
+    l.grid = dim3((unsigned)tma_blocks, 1, 1);
+    l.smem = tma_smem;
+  }
   return l;
 }
 
@@ -241,7 +255,7 @@ Launch lbm_sim::step_shape() const {
 // each plane z, its lattice tiles {z, t} (t = tile in the plane), then its
 // boundary tiles {-1 - count, first record}.
 int lbm_sim::ensure_tiles() {
-  if (tiles && tiles_bx == step_bx && tiles_by == step_by) return LBM_OK;
+  if (tiles && tiles_bx == step_bx && tiles_by == step_by && tiles_var == variant) return LBM_OK;
   const int tpb = step_bx * step_by;
   const int gx = nxp / step_bx, gy = (ny + step_by - 1) / step_by;
   std::vector<uint32_t> hc(np / 32 + 1, 0u);
@@ -267,6 +281,14 @@ int lbm_sim::ensure_tiles() {
   LBM_CUDA(this, cudaStreamSynchronize(stream));
   tiles_bx = step_bx;
   tiles_by = step_by;
+  tiles_var = variant;
+  if (variant == 4) {
+    cudaError_t e = prepare_step_tma(lattice, dtype, has_force, step_bx, step_by, ntiles, &tma_blocks, &tma_smem);
+    if (e != cudaSuccess) {
+      tiles_bx = 0;
+      return lbm_fail(this, LBM_ERR_CUDA, std::string("TMA-staged step: ") + cudaGetErrorString(e));
+    }
+  }
   return LBM_OK;
 }
 Launch lbm_sim::aux_shape() const { return shape(32, 8); }
@@ -536,7 +558,7 @@ int lbm_sim::download(HostGeometry &g) {
 // ---------------------------------------------------------------- launch configuration
 static bool valid_launch(const lbm_sim *h, int bx, int by, int variant, int tiles) {
   if (bx < 32 || bx % 32 || h->nxp % bx || by < 1 || bx * by > 256) return false;
-  if (variant < 0 || variant > 3 || tiles < 1 || tiles > 4) return false;
+  if (variant < 0 || variant > 4 || tiles < 1 || tiles > 4) return false;
   if (h->dtype == LBM_F64 && variant != 0) return false;
   return true;
 }
@@ -573,13 +595,14 @@ extern "C" int lbm_autotune(lbm_handle h, int steps, int *bx, int *by, int *vari
   int best[4] = {save[0], save[1], save[2], save[3]};
   float best_ms = 1e30f;
   int rc = LBM_OK;
-  const int nvar = h->dtype == LBM_F64 ? 1 : 4;
+  const int nvar = h->dtype == LBM_F64 ? 1 : 5;  // variant 4: TMA-staged persistent kernel
   const int tile_opts[3] = {1, 2, 4};
   for (int threads = 128; threads <= 256 && rc == LBM_OK; threads *= 2)
     for (int bxx = 32; bxx <= threads && rc == LBM_OK; bxx *= 2) {
       if (h->nxp % bxx) continue;
       for (int var = 0; var < nvar && rc == LBM_OK; ++var)
         for (int k = 0; k < 3 && rc == LBM_OK; ++k) {
+          if (var == 4 && k > 0) continue;  // the persistent kernel ignores tiles per block
           h->step_bx = bxx;
           h->step_by = threads / bxx;
           h->variant = var;

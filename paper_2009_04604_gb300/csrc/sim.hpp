@@ -62,6 +62,7 @@ struct lbm_sim {
   int has_uw = 0;
 
   double *dres = nullptr;     // reduction results (device)
+  int *err_dev = nullptr;     // device error word (bit 0: a bounded wait ran out)
   double *scratch = nullptr;  // per-block reduction partials (device)
   long long scratch_len = 0;
 
@@ -70,6 +71,8 @@ struct lbm_sim {
   long long ntiles = 0;
   int tiles_bx = 0, tiles_by = 0;  // launch shape the table was built for (0: stale)
   int tiles_per_block = 4;          // consecutive table entries per step-kernel block (1..4)
+  int tiles_var = -1;               // register variant the launch data was prepared for
+  int tma_blocks = 0, tma_smem = 0; // persistent grid and shared memory of the TMA-staged step
   int step_bx = 32, step_by = 8, variant = 0;
   bool geom_ok = false, state_ok = false;
   int version = 0;  // bumped whenever the kernel view changes (options, geometry)
