@@ -214,10 +214,15 @@ int lbm_get_counts(lbm_handle h, int64_t *n_fluid, int64_t *n_boundary, int64_t 
  *     length, bx*by <= 256;
  *   variant 0..3: the register budget. Variant v guarantees v+1 resident
  *     256-thread blocks per SM;
- *   variant 4: the TMA-staged persistent kernel. One thread per block copies
+ *   variant 4: the TMA-staged persistent kernel. The first warp of a block copies
  *     each lattice tile's source rows into shared memory with bulk asynchronous
  *     copies, several tiles ahead, and the block computes from there. FP32,
- *     FP16 and BF16 only. FP64 storage accepts variant 0 only;
+ *     FP16 and BF16 only;
+ *   variant 5..7: two nodes per thread along x, with vector loads and stores,
+ *     at least 1..3 resident blocks per SM. A block covers 2*bx nodes of a row,
+ *     which must divide the padded row. FP32/FP16/BF16, not with BFL (switching
+ *     to BFL moves the launch back to variant 0).
+ * FP64 storage accepts variant 0 only;
  *   tiles 1..4: consecutive entries of the step kernel's tile table that one
  *     block processes. The table lists, plane by plane, the lattice tiles and
  *     then the boundary-record tiles.

@@ -51,14 +51,14 @@ static cudaError_t dispatch(int lattice, int dtype, Fn &&fn) {
 }
 
 // The step grid is 1-D, one block per entry of the tile table (l.grid.x entries).
-template <class L, typename S, typename M, int MINB>
+template <class L, typename S, typename M, int MINB, bool PAIR = false>
 static cudaError_t step_variant(const View &v, const void *fin, void *fout, const Launch &l) {
   if (v.has_force)
-    k_step<L, S, M, MINB, true><<<l.grid, l.block, 0, l.stream>>>(v, static_cast<const S *>(fin),
-                                                                  static_cast<S *>(fout));
+    k_step<L, S, M, MINB, true, PAIR><<<l.grid, l.block, 0, l.stream>>>(v, static_cast<const S *>(fin),
+                                                                        static_cast<S *>(fout));
   else
-    k_step<L, S, M, MINB, false><<<l.grid, l.block, 0, l.stream>>>(v, static_cast<const S *>(fin),
-                                                                   static_cast<S *>(fout));
+    k_step<L, S, M, MINB, false, PAIR><<<l.grid, l.block, 0, l.stream>>>(v, static_cast<const S *>(fin),
+                                                                         static_cast<S *>(fout));
   return cudaGetLastError();
 }
 
@@ -141,6 +141,9 @@ cudaError_t launch_step(int lattice, int dtype, int variant, const View &v, cons
         case 1: return step_variant<L, S, M, 2>(v, fin, fout, l);
         case 2: return step_variant<L, S, M, 3>(v, fin, fout, l);
         case 3: return step_variant<L, S, M, 4>(v, fin, fout, l);
+        case 5: return step_variant<L, S, M, 1, true>(v, fin, fout, l);
+        case 6: return step_variant<L, S, M, 2, true>(v, fin, fout, l);
+        case 7: return step_variant<L, S, M, 3, true>(v, fin, fout, l);
         default: return step_variant<L, S, M, 1>(v, fin, fout, l);
       }
     }

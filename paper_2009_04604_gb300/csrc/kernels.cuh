@@ -147,9 +147,10 @@ __device__ __forceinline__ M post(const View &v, int i, const M fi, const Macro<
 // the even part is shared by the pair and the odd part flips sign, and
 // f*_i = (1 - omega) f_i + omega f^eq_i + S_i. The Guo source splits the same way:
 // S = k w (9 (c.u)(c.F) - 3 u.F) + 3 k w (c.F), with k = 1 - omega/2.
-template <class L, typename S, typename M, bool FORCE>
-__device__ __forceinline__ void collide_store(const View &v, const M (&f)[L::Q], const Macro<L, M> &m,
-                                              S *__restrict__ dst, int np) {
+// The relaxed value of direction i goes to put(i, value); collide_store writes it
+// to the output planes, post_all to registers.
+template <class L, typename M, bool FORCE, class Put>
+__device__ __forceinline__ void relax(const View &v, const M (&f)[L::Q], const Macro<L, M> &m, Put &&put) {
   constexpr int R = L::Q / 2;
   const Par<M> P(v);
   const M om = P.omega, omr = M(1) - om;
@@ -165,7 +166,7 @@ __device__ __forceinline__ void collide_store(const View &v, const M (&f)[L::Q],
     const M w = M(weight<L>(R));
     M eq = w * b0;
     if constexpr (FORCE) eq -= M(3) * kf * w * uF;
-    dst[R * np] = to_store<S, M>(omr * f[R] + eq);
+    put(R, omr * f[R] + eq);
   }
 #pragma unroll
   for (int i = 0; i < R; ++i) {
@@ -179,9 +180,21 @@ __device__ __forceinline__ void collide_store(const View &v, const M (&f)[L::Q],
       sym += kf * w * (M(9) * cu * cF - M(3) * uF);
       asym += M(3) * kf * w * cF;
     }
-    dst[i * np] = to_store<S, M>(omr * f[i] + (sym + asym));
-    dst[j * np] = to_store<S, M>(omr * f[j] + (sym - asym));
+    put(i, omr * f[i] + (sym + asym));
+    put(j, omr * f[j] + (sym - asym));
   }
+}
+
+template <class L, typename S, typename M, bool FORCE>
+__device__ __forceinline__ void collide_store(const View &v, const M (&f)[L::Q], const Macro<L, M> &m,
+                                              S *__restrict__ dst, int np) {
+  relax<L, M, FORCE>(v, f, m, [&](int i, M val) { dst[i * np] = to_store<S, M>(val); });
+}
+
+template <class L, typename M, bool FORCE>
+__device__ __forceinline__ void post_all(const View &v, const M (&f)[L::Q], const Macro<L, M> &m,
+                                         M (&out)[L::Q]) {
+  relax<L, M, FORCE>(v, f, m, [&](int i, M val) { out[i] = val; });
 }
 
 // ---------------------------------------------------------------- boundary rule
@@ -377,6 +390,119 @@ __device__ __forceinline__ void lattice_tile(const View &v, const S *__restrict_
   collide_store<L, S, M, FORCE>(v, f, m, fout + n, np);
 }
 
+// ---------------------------------------------------------------- two nodes per thread
+// Lattice tile {z, t} with bx threads covering 2 bx nodes of a row: thread tx owns
+// the aligned pair (x, x+1), x = x0 + 2 tx. One vector load per plane fetches the
+// pair at x of the plane's source row (y - c_iy, z - c_iz). A plane with c_ix = +1
+// needs (x-1, x), and x-1 is the upper element of the previous lane's pair. A plane
+// with c_ix = -1 needs (x+1, x+2), and x+2 is the lower element of the next lane's
+// pair. Lanes at the ends of the warp, and nodes whose source leaves [0, nx) (the
+// x wrap, with its shear), take one scalar load per such plane instead. All loads
+// are issued before any value is used, since a shuffle waits for its load. Both
+// nodes are then relaxed as in lattice_tile. A pair whose two nodes are fluid is
+// stored with one vector store per plane, otherwise node by node, so that the
+// slots of a non-fluid node (which may hold written-ahead values) are never
+// touched. Not used with BFL, whose record lookup assumes one node per lane.
+template <typename S> struct Vec2;
+template <> struct Vec2<float> {
+  using T = float2;
+  __device__ static float lo(T v) { return v.x; }
+  __device__ static float hi(T v) { return v.y; }
+  __device__ static T make(float a, float b) { return make_float2(a, b); }
+};
+template <> struct Vec2<__half> {
+  using T = __half2;
+  __device__ static float lo(T v) { return __low2float(v); }
+  __device__ static float hi(T v) { return __high2float(v); }
+  __device__ static T make(float a, float b) { return __floats2half2_rn(a, b); }
+};
+template <> struct Vec2<__nv_bfloat16> {
+  using T = __nv_bfloat162;
+  __device__ static float lo(T v) { return __low2float(v); }
+  __device__ static float hi(T v) { return __high2float(v); }
+  __device__ static T make(float a, float b) { return __floats2bfloat162_rn(a, b); }
+};
+
+template <class L, typename S, typename M, bool FORCE>
+__device__ __forceinline__ void lattice_tile_pair(const View &v, const S *__restrict__ fin,
+                                                  S *__restrict__ fout, int2 tile) {
+  using V = Vec2<S>;
+  using T = typename V::T;
+  const int lane = threadIdx.x & 31;
+  const int x = (tile.y % v.gx) * (2 * blockDim.x) + 2 * threadIdx.x;
+  const int y = (tile.y / v.gx) * blockDim.y + threadIdx.y;
+  const int z = tile.x;
+  if (y >= v.ny) return;  // uniform across the warp
+  const int n = (z * v.ny + y) * v.nxp + x;
+  const uint16_t fl2 = *reinterpret_cast<const uint16_t *>(v.flags + n);
+  const bool fa = (fl2 & 3) == K_FLUID, fb = ((fl2 >> 8) & 3) == K_FLUID;
+  if (!__any_sync(0xffffffffu, fa || fb)) return;  // the whole warp is idle
+  // offsets of the 9 (dy, dz) source rows, without the x wrap
+  const int plane = v.nxp * v.ny;
+  int ro[3][3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      int yy = y + b - 1, zz = z + c - 1;
+      yy = yy < 0 ? yy + v.ny : (yy >= v.ny ? yy - v.ny : yy);
+      zz = zz < 0 ? zz + v.nz : (zz >= v.nz ? zz - v.nz : zz);
+      ro[b][c] = (zz - z) * plane + (yy - y) * v.nxp;
+    }
+  const int np = (int)v.np;
+  T p[L::Q];
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i)
+    p[i] = __ldg(reinterpret_cast<const T *>(fin + (long long)i * np + n + ro[1 - L::cy(i)][1 - L::cz(i)]));
+  // the element per x-shifted plane that the neighbouring lanes cannot supply:
+  // c_ix = +1: x-1 at lane 0 (wrapping when x = 0); c_ix = -1: x+1 when it leaves
+  // the row (node x+1 is then padding), else x+2 at lane 31 or when it wraps
+  const bool wa = x + 1 >= v.nx;
+  const bool need_up = lane == 0, need_dn = wa || lane == 31 || x + 2 >= v.nx;
+  M e[L::Q];
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    const int cx = L::cx(i);
+    e[i] = M(0);
+    if (cx > 0 && need_up)
+      e[i] = to_math<S, M>(__ldg(fin + (long long)i * np + n + upstream_offset(v, x, y, z, cx, L::cy(i), L::cz(i))));
+    if (cx < 0 && need_dn) {
+      const int off = wa ? upstream_offset(v, x, y, z, cx, L::cy(i), L::cz(i))
+                         : 1 + upstream_offset(v, x + 1, y, z, cx, L::cy(i), L::cz(i));
+      e[i] = to_math<S, M>(__ldg(fin + (long long)i * np + n + off));
+    }
+  }
+  M f0[L::Q], f1[L::Q];
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    const int cx = L::cx(i);
+    if (cx == 0) {
+      f0[i] = V::lo(p[i]);
+      f1[i] = V::hi(p[i]);
+    } else if (cx > 0) {  // sources x-1, x
+      const M prev = __shfl_up_sync(0xffffffffu, V::hi(p[i]), 1);
+      f0[i] = need_up ? e[i] : prev;
+      f1[i] = V::lo(p[i]);
+    } else {  // sources x+1, x+2
+      const M next = __shfl_down_sync(0xffffffffu, V::lo(p[i]), 1);
+      f0[i] = wa ? e[i] : V::hi(p[i]);
+      f1[i] = need_dn && !wa ? e[i] : next;
+    }
+  }
+  if (fa && fb) {
+    const Macro<L, M> ma = moments<L, M>(v, f0), mb = moments<L, M>(v, f1);
+    M pa[L::Q], pb[L::Q];
+    post_all<L, M, FORCE>(v, f0, ma, pa);
+    post_all<L, M, FORCE>(v, f1, mb, pb);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+      *reinterpret_cast<T *>(fout + (long long)i * np + n) = V::make(pa[i], pb[i]);
+  } else {
+    if (fa) collide_store<L, S, M, FORCE>(v, f0, moments<L, M>(v, f0), fout + n, np);
+    if (fb) collide_store<L, S, M, FORCE>(v, f1, moments<L, M>(v, f1), fout + n + 1, np);
+  }
+}
+
 // Boundary tile: one thread per boundary record. {-1 - count, first} takes static
 // records first .. first+count-1. {DYN_TILE, first} takes the moving body's
 // records first .. first+blocksize-1 that exist in this step (their number is
@@ -402,7 +528,7 @@ __device__ __forceinline__ void boundary_tile(const View &v, const S *__restrict
 
 // Block b takes table entries b*T .. b*T+T-1 (T = v.tpb_tiles <= 4), whose
 // descriptors it loads together up front.
-template <class L, typename S, typename M, int MINB, bool FORCE>
+template <class L, typename S, typename M, int MINB, bool FORCE, bool PAIR = false>
 __global__ void __launch_bounds__(256, MINB) k_step(const View v, const S *__restrict__ fin,
                                                     S *__restrict__ fout) {
   __shared__ M stage[L::Q * 256];  // boundary tiles: populations, [direction][thread]
@@ -416,6 +542,7 @@ __global__ void __launch_bounds__(256, MINB) k_step(const View v, const S *__res
   for (int k = 0; k < 4; ++k) {
     if (k >= T || first + k >= v.ntiles) break;
     if (tl[k].x < 0) boundary_tile<L, S, M>(v, fin, fout, tl[k], stage);
+    else if constexpr (PAIR) lattice_tile_pair<L, S, M, FORCE>(v, fin, fout, tl[k]);
     else lattice_tile<L, S, M, FORCE>(v, fin, fout, tl[k]);
   }
 }

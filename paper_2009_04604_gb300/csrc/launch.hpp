@@ -22,8 +22,9 @@ cudaError_t prepare_step_tma(int lattice, int dtype, int has_force, int bx, int 
 
 // lattice: 0 D2Q9, 1 D3Q19; dtype: 0 F64, 1 F32, 2 F16, 3 BF16
 // variant: register budget of the step kernel, at least variant+1 resident
-// 256-thread blocks per SM (0..3), or 4: the TMA-staged persistent kernel
-// (FP32/FP16/BF16). FP64 has a single variant.
+// 256-thread blocks per SM (0..3), 4: the TMA-staged persistent kernel, or 5..7:
+// two nodes per thread with at least 1..3 resident blocks per SM (FP32/FP16/BF16).
+// FP64 has a single variant.
 cudaError_t launch_step(int lattice, int dtype, int variant, const View &v, const void *fin,
                         void *fout, const Launch &l);
 cudaError_t launch_init(int lattice, int dtype, const View &v, void *fout, double rho, double ux,

@@ -183,6 +183,7 @@ extern "C" int lbm_set_options(lbm_handle h, int bc, double rho0, const double f
     if (e != cudaSuccess) { h->bc = old_bc; return lbm_fail(h, LBM_ERR_CUDA, cudaGetErrorString(e)); }
   }
   h->bc = bc;
+  if (bc == LBM_BC_BFL && h->variant >= 5) { h->variant = 0; h->tune_default(); }  // pairs have no BFL path
   h->rho0 = rho0;
   h->has_force = 0;
   for (int a = 0; a < 3; ++a) {
@@ -209,7 +210,7 @@ View lbm_sim::view() const {
   for (int a = 0; a < 3; ++a) v.F_f[a] = (float)F[a];
   v.flags = flags; v.cbase = cbase; v.rec = rec; v.rnode = rnode; v.nb = nb;
   v.err = err_dev;
-  v.tiles = tiles; v.gx = nxp / step_bx;
+  v.tiles = tiles; v.gx = nxp / (step_bx * npt());
   v.ntiles = (int)ntiles; v.tpb_tiles = tiles_per_block;
   if (mb.on) {
     v.dyn = RecSet{mb.rec[cur], mb.rnode[cur], mb.lq[cur], mb.luw[cur], mb.luw1[cur], mb.ltag[cur]};
@@ -257,7 +258,7 @@ Launch lbm_sim::step_shape() const {
 int lbm_sim::ensure_tiles() {
   if (tiles && tiles_bx == step_bx && tiles_by == step_by && tiles_var == variant) return LBM_OK;
   const int tpb = step_bx * step_by;
-  const int gx = nxp / step_bx, gy = (ny + step_by - 1) / step_by;
+  const int gx = nxp / (step_bx * npt()), gy = (ny + step_by - 1) / step_by;
   std::vector<uint32_t> hc(np / 32 + 1, 0u);
   if (nb > 0)
     LBM_CUDA(this, cudaMemcpyAsync(hc.data(), cbase, hc.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
@@ -558,8 +559,9 @@ int lbm_sim::download(HostGeometry &g) {
 // ---------------------------------------------------------------- launch configuration
 static bool valid_launch(const lbm_sim *h, int bx, int by, int variant, int tiles) {
   if (bx < 32 || bx % 32 || h->nxp % bx || by < 1 || bx * by > 256) return false;
-  if (variant < 0 || variant > 4 || tiles < 1 || tiles > 4) return false;
+  if (variant < 0 || variant > 7 || tiles < 1 || tiles > 4) return false;
   if (h->dtype == LBM_F64 && variant != 0) return false;
+  if (variant >= 5 && (h->nxp % (2 * bx) || h->bc == LBM_BC_BFL)) return false;  // pairs: whole rows, no BFL
   return true;
 }
 
@@ -595,7 +597,7 @@ extern "C" int lbm_autotune(lbm_handle h, int steps, int *bx, int *by, int *vari
   int best[4] = {save[0], save[1], save[2], save[3]};
   float best_ms = 1e30f;
   int rc = LBM_OK;
-  const int nvar = h->dtype == LBM_F64 ? 1 : 5;  // variant 4: TMA-staged persistent kernel
+  const int nvar = h->dtype == LBM_F64 ? 1 : 8;  // 4: TMA-staged persistent kernel; 5-7: node pairs
   const int tile_opts[3] = {1, 2, 4};
   for (int threads = 128; threads <= 256 && rc == LBM_OK; threads *= 2)
     for (int bxx = 32; bxx <= threads && rc == LBM_OK; bxx *= 2) {
@@ -603,6 +605,7 @@ extern "C" int lbm_autotune(lbm_handle h, int steps, int *bx, int *by, int *vari
       for (int var = 0; var < nvar && rc == LBM_OK; ++var)
         for (int k = 0; k < 3 && rc == LBM_OK; ++k) {
           if (var == 4 && k > 0) continue;  // the persistent kernel ignores tiles per block
+          if (!valid_launch(h, bxx, threads / bxx, var, tile_opts[k])) continue;
           h->step_bx = bxx;
           h->step_by = threads / bxx;
           h->variant = var;

@@ -79,6 +79,7 @@ struct lbm_sim {
   MovingBody mb;
   std::string err;
 
+  int npt() const { return variant >= 5 ? 2 : 1; }  // nodes per thread along x in lattice tiles
   size_t elem_size() const;
   size_t link_size() const;
   void lattice_c(int i, int &x, int &y, int &z) const;
