@@ -312,6 +312,11 @@ __device__ void boundary(const View &v, const RecSet &rs, const Rec &r, const M 
   }
 }
 
+// non-binding request to bring the line holding p into L1
+__device__ __forceinline__ void prefetch_l1(const void *p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 // The boundary work of one boundary node: the node's own pre-collision
 // populations (gathered from fin, which is unchanged during the step, and
 // BFL-completed), its moments, and the written-ahead unknowns of its wall and
@@ -320,6 +325,20 @@ template <class L, typename S, typename M>
 __device__ __forceinline__ void boundary_node(const View &v, const RecSet &rs, const Rec r,
                                               const S *__restrict__ fin, S *__restrict__ fout, long long n,
                                               int x, int y, int z, M *fs, int stride) {
+  // The link loop reads q (and the wall velocities) one link after another. Ask
+  // for the record's contiguous link data now, so that it is in L1 by then and
+  // the loop does not wait on memory once per link.
+  if (r.cut) {
+    const uint32_t l0 = r.link0, l1 = r.link0 + __popc(r.cut) - 1u;
+    prefetch_l1(static_cast<const M *>(rs.lq) + l0);
+    prefetch_l1(static_cast<const M *>(rs.lq) + l1);
+    if (rs.luw != nullptr && (r.open & REC_MOVING)) {
+      prefetch_l1(static_cast<const M *>(rs.luw) + 3 * l0);
+      prefetch_l1(static_cast<const M *>(rs.luw) + 3 * l1 + 2);
+      prefetch_l1(static_cast<const M *>(rs.luw1) + 3 * l0);
+      prefetch_l1(static_cast<const M *>(rs.luw1) + 3 * l1 + 2);
+    }
+  }
   Nbr nb;
   nb.init(v, x, y, z);
   M f[L::Q];
@@ -489,17 +508,22 @@ __device__ __forceinline__ void lattice_tile_pair(const View &v, const S *__rest
       f1[i] = need_dn && !wa ? e[i] : next;
     }
   }
+  // every lane relaxes both nodes (a non-fluid node's values are discarded), so
+  // that only the stores of pairs with a non-fluid node diverge
+  const Macro<L, M> ma = moments<L, M>(v, f0), mb = moments<L, M>(v, f1);
+  M pa[L::Q], pb[L::Q];
+  post_all<L, M, FORCE>(v, f0, ma, pa);
+  post_all<L, M, FORCE>(v, f1, mb, pb);
   if (fa && fb) {
-    const Macro<L, M> ma = moments<L, M>(v, f0), mb = moments<L, M>(v, f1);
-    M pa[L::Q], pb[L::Q];
-    post_all<L, M, FORCE>(v, f0, ma, pa);
-    post_all<L, M, FORCE>(v, f1, mb, pb);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i)
       *reinterpret_cast<T *>(fout + (long long)i * np + n) = V::make(pa[i], pb[i]);
   } else {
-    if (fa) collide_store<L, S, M, FORCE>(v, f0, moments<L, M>(v, f0), fout + n, np);
-    if (fb) collide_store<L, S, M, FORCE>(v, f1, moments<L, M>(v, f1), fout + n + 1, np);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      if (fa) fout[(long long)i * np + n] = to_store<S, M>(pa[i]);
+      if (fb) fout[(long long)i * np + n + 1] = to_store<S, M>(pb[i]);
+    }
   }
 }
 
