@@ -1,7 +1,9 @@
 """Build liblbm.so (CUDA, sm_103a) in-tree: paper_2009_04604_gb300/_build/liblbm.so.
 
 Each translation unit compiles in its own nvcc process, in parallel; the objects
-are linked with ``nvcc -shared`` (static CUDA runtime). No cmake.
+are linked with ``nvcc -shared`` (static CUDA runtime). No cmake. The fused step
+kernel, step_inst.cu, is compiled once per (lattice, storage type), since its
+instantiations dominate the build time.
 """
 from __future__ import annotations
 
@@ -22,6 +24,8 @@ COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC", "--exp
                  "-I", INCLUDE]
 # per-file extra flags: the geometry kernels round like the plain FP64 definitions
 EXTRA = {"geometry.cu": ["-fmad=false"]}
+# step_inst.cu: one object per (lattice, storage type)
+STEP_INSTANCES = [(lat, sto) for lat in ("D2Q9", "D3Q19") for sto in ("double", "float", "__half", "__nv_bfloat16")]
 
 
 def _nvcc():
@@ -53,18 +57,30 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     srcs = _sources()
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc] + COMMON + EXTRA.get(src, []) + ["-c", os.path.join(CSRC, src), "-o", obj]
+    jobs = []
+    for src in srcs:
+        if src == "step_inst.cu":
+            for lat, sto in STEP_INSTANCES:
+                jobs.append((src, [f"-DLBM_STEP_LATTICE={lat}", f"-DLBM_STEP_STORE={sto}"],
+                             f"step_{lat}_{sto.strip('_')}.o"))
+        else:
+            jobs.append((src, EXTRA.get(src, []), src.replace(".cu", ".o")))
+    # the slowest units first, so that they overlap with the rest
+    jobs.sort(key=lambda j: j[0] != "step_inst.cu")
+
+    def compile_one(job):
+        src, flags, name = job
+        obj = os.path.join(BUILD, name)
+        cmd = [nvcc] + COMMON + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
-            raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
+            raise RuntimeError(f"nvcc failed on {src} {' '.join(flags)}:\n{r.stderr}")
         if verbose and r.stderr:
             sys.stderr.write(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(compile_one, srcs))
+    with ThreadPoolExecutor(max_workers=min(os.cpu_count() or 8, len(jobs))) as ex:
+        objs = list(ex.map(compile_one, jobs))
     tmp = LIB + f".tmp{os.getpid()}"
     r = subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)
     if r.returncode != 0:

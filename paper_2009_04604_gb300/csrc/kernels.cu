@@ -1,6 +1,5 @@
 // kernels.cu -- instantiation and dispatch of the lattice Boltzmann kernels.
-#include "kernels.cuh"
-#include "launch.hpp"
+#include "step.cuh"
 
 namespace lbm {
 
@@ -50,103 +49,19 @@ static cudaError_t dispatch(int lattice, int dtype, Fn &&fn) {
   return cudaErrorInvalidValue;
 }
 
-// The step grid is 1-D, one block per entry of the tile table (l.grid.x entries).
-template <class L, typename S, typename M, int MINB, bool PAIR = false>
-static cudaError_t step_variant(const View &v, const void *fin, void *fout, const Launch &l) {
-  if (v.has_force)
-    k_step<L, S, M, MINB, true, PAIR><<<l.grid, l.block, 0, l.stream>>>(v, static_cast<const S *>(fin),
-                                                                        static_cast<S *>(fout));
-  else
-    k_step<L, S, M, MINB, false, PAIR><<<l.grid, l.block, 0, l.stream>>>(v, static_cast<const S *>(fin),
-                                                                         static_cast<S *>(fout));
-  return cudaGetLastError();
-}
-
-// Shared-memory bytes of one stage of the TMA-staged step: the rows of every
-// population plane with a 16-byte halo on each side, the flag rows, and at least
-// the boundary tiles' staging array.
-template <class L, typename S, typename M>
-static int tma_stage_bytes(int bx, int by) {
-  const int halo = 16 / (int)sizeof(S);
-  const int pops = L::Q * by * (bx + 2 * halo) * (int)sizeof(S);
-  const int need = pops + bx * by;
-  const int stagebnd = L::Q * 256 * (int)sizeof(M);
-  const int b = need > stagebnd ? need : stagebnd;
-  return (b + 127) / 128 * 128;
-}
-
-// Two persistent blocks per SM, each with as many stages as half of the shared
-// memory allows (at most 16): the copies in flight, not registers, then set the
-// memory-level parallelism.
-static int tma_stages(int stage_bytes, int optin) {
-  int k = (optin / 2 - 128) / stage_bytes;
-  return k > 16 ? 16 : k;
-}
-
-template <class L, typename S, typename M, bool FORCE>
-static cudaError_t tma_prepare(int bx, int by, long long ntiles, int *blocks, int *smem) {
-  const int sb = tma_stage_bytes<L, S, M>(bx, by);
-  int dev0 = 0, optin = 0;
-  cudaError_t e0 = cudaGetDevice(&dev0);
-  if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev0);
-  if (e0 != cudaSuccess) return e0;
-  const int stages = tma_stages(sb, optin);
-  if (stages < 2) return cudaErrorInvalidConfiguration;
-  *smem = 128 + stages * sb;
-  auto kern = k_step_tma<L, S, M, FORCE>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
-  if (e != cudaSuccess) return e;
-  int dev = 0, nsm = 0, per = 0;
-  e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, bx * by, *smem);
-  if (e != cudaSuccess) return e;
-  if (per < 1) return cudaErrorInvalidConfiguration;
-  long long b = (long long)nsm * per;
-  if (b > ntiles) b = ntiles;
-  *blocks = (int)(b < 1 ? 1 : b);
-  return cudaSuccess;
-}
+LBM_STEP_INSTANCES(LBM_STEP_DECLARE)
 
 cudaError_t prepare_step_tma(int lattice, int dtype, int has_force, int bx, int by, long long ntiles,
                              int *blocks, int *smem) {
   return dispatch(lattice, dtype, [&]<class L, typename S, typename M>() {
-    if constexpr (sizeof(M) == 8) {
-      return cudaErrorInvalidValue;  // FP64 has no TMA-staged variant
-    } else {
-      return has_force ? tma_prepare<L, S, M, true>(bx, by, ntiles, blocks, smem)
-                       : tma_prepare<L, S, M, false>(bx, by, ntiles, blocks, smem);
-    }
+    return prepare_step_tma_ls<L, S>(has_force, bx, by, ntiles, blocks, smem);
   });
-}
-
-template <class L, typename S, typename M, bool FORCE>
-static cudaError_t tma_launch(const View &v, const void *fin, void *fout, const Launch &l) {
-  const int sb = tma_stage_bytes<L, S, M>(l.block.x, l.block.y);
-  const int stages = (l.smem - 128) / sb;
-  k_step_tma<L, S, M, FORCE><<<l.grid, l.block, l.smem, l.stream>>>(
-      v, static_cast<const S *>(fin), static_cast<S *>(fout), stages, sb);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_step(int lattice, int dtype, int variant, const View &v, const void *fin,
                         void *fout, const Launch &l) {
   return dispatch(lattice, dtype, [&]<class L, typename S, typename M>() {
-    if constexpr (sizeof(M) == 8) {
-      return step_variant<L, S, M, 1>(v, fin, fout, l);  // FP64: one register budget
-    } else {
-      if (variant == 4)
-        return v.has_force ? tma_launch<L, S, M, true>(v, fin, fout, l) : tma_launch<L, S, M, false>(v, fin, fout, l);
-      switch (variant) {
-        case 1: return step_variant<L, S, M, 2>(v, fin, fout, l);
-        case 2: return step_variant<L, S, M, 3>(v, fin, fout, l);
-        case 3: return step_variant<L, S, M, 4>(v, fin, fout, l);
-        case 5: return step_variant<L, S, M, 1, true>(v, fin, fout, l);
-        case 6: return step_variant<L, S, M, 2, true>(v, fin, fout, l);
-        case 7: return step_variant<L, S, M, 3, true>(v, fin, fout, l);
-        default: return step_variant<L, S, M, 1>(v, fin, fout, l);
-      }
-    }
+    return launch_step_ls<L, S>(variant, v, fin, fout, l);
   });
 }
 

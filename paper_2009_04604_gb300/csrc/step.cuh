@@ -1,0 +1,126 @@
+// step.cuh -- launch of the fused step kernel for one (lattice, storage type).
+//
+// The step kernel has many instantiations (register budget, node pairs, force
+// path, the TMA-staged kernel). They are compiled in one translation unit per
+// (lattice, storage type), step_inst.cu built once for each pair, so that the
+// build runs them in parallel. kernels.cu dispatches to the explicit
+// instantiations of launch_step_ls and prepare_step_tma_ls.
+#pragma once
+
+#include "kernels.cuh"
+#include "launch.hpp"
+
+namespace lbm {
+
+// The step grid is 1-D, one block per entry of the tile table (l.grid.x entries).
+template <class L, typename S, typename M, int MINB, bool PAIR = false>
+cudaError_t step_variant(const View &v, const void *fin, void *fout, const Launch &l) {
+  if (v.has_force)
+    k_step<L, S, M, MINB, true, PAIR><<<l.grid, l.block, 0, l.stream>>>(v, static_cast<const S *>(fin),
+                                                                        static_cast<S *>(fout));
+  else
+    k_step<L, S, M, MINB, false, PAIR><<<l.grid, l.block, 0, l.stream>>>(v, static_cast<const S *>(fin),
+                                                                         static_cast<S *>(fout));
+  return cudaGetLastError();
+}
+
+// Shared-memory bytes of one stage of the TMA-staged step: the rows of every
+// population plane with a 16-byte halo on each side, the flag rows, and at least
+// the boundary tiles' staging array.
+template <class L, typename S, typename M>
+int tma_stage_bytes(int bx, int by) {
+  const int halo = 16 / (int)sizeof(S);
+  const int pops = L::Q * by * (bx + 2 * halo) * (int)sizeof(S);
+  const int need = pops + bx * by;
+  const int stagebnd = L::Q * 256 * (int)sizeof(M);
+  const int b = need > stagebnd ? need : stagebnd;
+  return (b + 127) / 128 * 128;
+}
+
+// Two persistent blocks per SM, each with as many stages as half of the shared
+// memory allows (at most 16): the copies in flight, not registers, then set the
+// memory-level parallelism.
+inline int tma_stages(int stage_bytes, int optin) {
+  int k = (optin / 2 - 128) / stage_bytes;
+  return k > 16 ? 16 : k;
+}
+
+template <class L, typename S, typename M, bool FORCE>
+cudaError_t tma_prepare(int bx, int by, long long ntiles, int *blocks, int *smem) {
+  const int sb = tma_stage_bytes<L, S, M>(bx, by);
+  int dev0 = 0, optin = 0;
+  cudaError_t e0 = cudaGetDevice(&dev0);
+  if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev0);
+  if (e0 != cudaSuccess) return e0;
+  const int stages = tma_stages(sb, optin);
+  if (stages < 2) return cudaErrorInvalidConfiguration;
+  *smem = 128 + stages * sb;
+  auto kern = k_step_tma<L, S, M, FORCE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0, per = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, bx * by, *smem);
+  if (e != cudaSuccess) return e;
+  if (per < 1) return cudaErrorInvalidConfiguration;
+  long long b = (long long)nsm * per;
+  if (b > ntiles) b = ntiles;
+  *blocks = (int)(b < 1 ? 1 : b);
+  return cudaSuccess;
+}
+
+template <class L, typename S, typename M, bool FORCE>
+cudaError_t tma_launch(const View &v, const void *fin, void *fout, const Launch &l) {
+  const int sb = tma_stage_bytes<L, S, M>(l.block.x, l.block.y);
+  const int stages = (l.smem - 128) / sb;
+  k_step_tma<L, S, M, FORCE><<<l.grid, l.block, l.smem, l.stream>>>(
+      v, static_cast<const S *>(fin), static_cast<S *>(fout), stages, sb);
+  return cudaGetLastError();
+}
+
+// Storage type S of lattice L: M is the arithmetic type (FP64 for FP64 storage).
+template <typename S> struct MathOf { using T = float; };
+template <> struct MathOf<double> { using T = double; };
+
+template <class L, typename S>
+cudaError_t launch_step_ls(int variant, const View &v, const void *fin, void *fout, const Launch &l) {
+  using M = typename MathOf<S>::T;
+  if constexpr (sizeof(M) == 8) {
+    return step_variant<L, S, M, 1>(v, fin, fout, l);  // FP64: one register budget
+  } else {
+    if (variant == 4)
+      return v.has_force ? tma_launch<L, S, M, true>(v, fin, fout, l) : tma_launch<L, S, M, false>(v, fin, fout, l);
+    switch (variant) {
+      case 1: return step_variant<L, S, M, 2>(v, fin, fout, l);
+      case 2: return step_variant<L, S, M, 3>(v, fin, fout, l);
+      case 3: return step_variant<L, S, M, 4>(v, fin, fout, l);
+      case 5: return step_variant<L, S, M, 1, true>(v, fin, fout, l);
+      case 6: return step_variant<L, S, M, 2, true>(v, fin, fout, l);
+      case 7: return step_variant<L, S, M, 3, true>(v, fin, fout, l);
+      default: return step_variant<L, S, M, 1>(v, fin, fout, l);
+    }
+  }
+}
+
+template <class L, typename S>
+cudaError_t prepare_step_tma_ls(int has_force, int bx, int by, long long ntiles, int *blocks, int *smem) {
+  using M = typename MathOf<S>::T;
+  if constexpr (sizeof(M) == 8) {
+    return cudaErrorInvalidValue;  // FP64 has no TMA-staged variant
+  } else {
+    return has_force ? tma_prepare<L, S, M, true>(bx, by, ntiles, blocks, smem)
+                     : tma_prepare<L, S, M, false>(bx, by, ntiles, blocks, smem);
+  }
+}
+
+#define LBM_STEP_INSTANCES(X) \
+  X(D2Q9, double) X(D2Q9, float) X(D2Q9, __half) X(D2Q9, __nv_bfloat16) \
+  X(D3Q19, double) X(D3Q19, float) X(D3Q19, __half) X(D3Q19, __nv_bfloat16)
+
+#define LBM_STEP_DECLARE(Lat, Sto)                                                                  \
+  extern template cudaError_t launch_step_ls<Lat, Sto>(int, const View &, const void *, void *,    \
+                                                       const Launch &);                           \
+  extern template cudaError_t prepare_step_tma_ls<Lat, Sto>(int, int, int, long long, int *, int *);
+
+}  // namespace lbm
