@@ -28,6 +28,7 @@ D2Q9, D3Q19 = 0, 1
 FLUID, SOLID, OPEN = 0, 1, 2
 BC_ELIBB_F, BC_ELIBB_FQ, BC_BFL, BC_HWBB, BC_ELIBB_U, BC_ELIBB_UQ = 0, 1, 2, 3, 4, 5
 SHAPE_SPHERE, SHAPE_SPHERE_OUT, SHAPE_ELLIPSOID, SHAPE_STRIP = 0, 1, 2, 3
+COLL_BGK, COLL_TRT = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -52,7 +53,7 @@ class Params(ctypes.Structure):
                 ("tau", ctypes.c_double), ("rho0", ctypes.c_double),
                 ("force", ctypes.c_double * 3), ("qcut", ctypes.c_double),
                 ("wall_neq_same", ctypes.c_int), ("me_rho0", ctypes.c_int),
-                ("s1_exact", ctypes.c_int)]
+                ("s1_exact", ctypes.c_int), ("collision", ctypes.c_int), ("magic", ctypes.c_double)]
 
 
 class Shape(ctypes.Structure):
@@ -106,7 +107,7 @@ def lattice(lat: int):
 
 
 def params(lattice_id, dims, tau, bc=BC_ELIBB_F, rho0=1.0, force=(0.0, 0.0, 0.0), xshift=0,
-           qcut=0.01, wall_neq_same=0, me_rho0=0, s1_exact=0) -> Params:
+           qcut=0.01, wall_neq_same=0, me_rho0=0, s1_exact=0, collision=0, magic=0.1875) -> Params:
     nx, ny, nz = (list(dims) + [1, 1])[:3]
     p = Params()
     p.lattice, p.nx, p.ny, p.nz, p.xshift, p.bc = lattice_id, nx, ny, nz, xshift, bc
@@ -114,6 +115,7 @@ def params(lattice_id, dims, tau, bc=BC_ELIBB_F, rho0=1.0, force=(0.0, 0.0, 0.0)
     for a in range(3):
         p.force[a] = float(force[a])
     p.wall_neq_same, p.me_rho0, p.s1_exact = wall_neq_same, me_rho0, s1_exact
+    p.collision, p.magic = collision, magic
     return p
 
 

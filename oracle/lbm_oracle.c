@@ -9,6 +9,7 @@
  * Paper: arXiv:2009.04604 (ELIBB single-node boundary condition).
  *   Lattice Boltzmann equation ............ Sec. II.A, Eq. LBE
  *   BGK collision, Omega = 1/tau .......... Sec. II.A, Eq. LB-BGK
+ *   TRT collision (even/odd rates) ........ Sec. II.A, TRT paragraph, Eq. magic-parameter
  *   second-order equilibrium .............. Sec. II.A, Eq. Eq2ndOrder (c_s^2 = 1/3)
  *   generic interpolated bounce-back ...... Sec. II.B, Eq. general-ibb-linear
  *   BFL (linear Bouzidi) .................. Sec. II.B, Eq. bfl
@@ -26,6 +27,10 @@
  *   - ELIBB-F weights are the Lagrange weights of Eq. poli_coeff at the points of
  *     Eq. x_to_s_helper (the printed q >= 1/2 weight (2-2q)/q is not a partition of unity);
  *   - the post-collision wall population uses (1 - 1/tau) f^neq, at s = 1;
+ *     under TRT as well (omega+ = 1/tau: the wall non-equilibrium is even in c
+ *     at first order);
+ *   - TRT with Guo forcing: the even and odd parts of the forcing term take the
+ *     factors (1 - omega+/2) and (1 - omega-/2);
  *   - the wall population index is i (incoming), as the paper's macros write it;
  *   - rho in the wall equilibria and the moving-wall term is rho_F(t);
  *   - the force uses the outgoing post-collision population f*_ibar (Wen et al.);
@@ -117,13 +122,32 @@ static double feq(const lat_t *L, int i, double rho, const double u[3]) {
   return L->w[i] * rho * (1.0 + cu / CS2 + quad / (2.0 * CS2 * CS2));
 }
 
-/* Guo forcing source: (1 - 1/(2 tau)) w_i [(c_i - u)/cs2 + (c_i.u) c_i/cs2^2] . F */
-static double guo_source(const lat_t *L, int i, double tau, const double u[3], const double F[3]) {
+/* Guo forcing term without its relaxation factor: w_i [(c_i - u)/cs2 + (c_i.u) c_i/cs2^2] . F */
+static double guo_term(const lat_t *L, int i, const double u[3], const double F[3]) {
   double cu = 0.0, s = 0.0;
   for (int a = 0; a < 3; ++a) cu += L->c[i][a] * u[a];
   for (int a = 0; a < 3; ++a)
     s += ((L->c[i][a] - u[a]) / CS2 + cu * L->c[i][a] / (CS2 * CS2)) * F[a];
-  return (1.0 - 1.0 / (2.0 * tau)) * L->w[i] * s;
+  return L->w[i] * s;
+}
+
+/* Guo forcing source of BGK: (1 - 1/(2 tau)) times the term above */
+static double guo_source(const lat_t *L, int i, double tau, const double u[3], const double F[3]) {
+  return (1.0 - 1.0 / (2.0 * tau)) * guo_term(L, i, u, F);
+}
+
+/* TRT collision of population i (Sec. II.A): the even parts a+ = (a_i + a_ibar)/2 of
+ * f, f^eq and the forcing term relax with omega+, the odd parts a- = (a_i - a_ibar)/2
+ * with omega-, each forcing part scaled by (1 - omega/2) of its own rate. */
+static double trt_post(const lat_t *L, int i, const double *fn, double rho, const double u[3],
+                       const double F[3], double omp, double omm) {
+  const int ib = L->opp[i];
+  const double fp = 0.5 * (fn[i] + fn[ib]), fm = 0.5 * (fn[i] - fn[ib]);
+  const double ei = feq(L, i, rho, u), eb = feq(L, ib, rho, u);
+  const double ep = 0.5 * (ei + eb), em = 0.5 * (ei - eb);
+  const double si = guo_term(L, i, u, F), sb = guo_term(L, ib, u, F);
+  const double sp = 0.5 * (si + sb), sm = 0.5 * (si - sb);
+  return fn[i] - omp * (fp - ep) - omm * (fm - em) + (1.0 - 0.5 * omp) * sp + (1.0 - 0.5 * omm) * sm;
 }
 
 /* density and Guo-corrected velocity u = (sum c f + F/2) / rho */
@@ -232,6 +256,10 @@ int or_step(const or_params *p, const uint8_t *flags, const double *q, const dou
   const int nx = p->nx, ny = p->ny, nz = p->nz;
   const long N = (long)nx * ny * nz;
   const double omega = 1.0 / p->tau;
+  const int trt = p->collision == OR_COLL_TRT;
+  if (trt && !(p->magic > 0.0)) return -1;
+  /* Eq. magic-parameter solved for omega- */
+  const double omega_m = trt ? 1.0 / (0.5 + p->magic / (p->tau - 0.5)) : omega;
   if (!uw1) uw1 = uw;
 
   double *fpost = (double *)calloc((size_t)N * Q, sizeof(double));
@@ -249,7 +277,8 @@ int or_step(const or_params *p, const uint8_t *flags, const double *q, const dou
     for (int a = 0; a < 3; ++a) vel[n * 3 + a] = u[a];
     for (int i = 0; i < Q; ++i) {
       double fi = f[n * Q + i];
-      fpost[n * Q + i] = fi - omega * (fi - feq(&L, i, r, u)) + guo_source(&L, i, p->tau, u, p->force);
+      fpost[n * Q + i] = trt ? trt_post(&L, i, f + n * Q, r, u, p->force, omega, omega_m)
+                             : fi - omega * (fi - feq(&L, i, r, u)) + guo_source(&L, i, p->tau, u, p->force);
     }
   }
 
@@ -296,6 +325,8 @@ int or_step(const or_params *p, const uint8_t *flags, const double *q, const dou
       const double rme = p->me_rho0 ? p->rho0 : rF;
       const double me = 2.0 * L.w[i] * rme * cu / CS2;
       /* wall populations (Eqs. f=eq+neq, ELIBB-approximation-eq1/eq2, neqbb-s) */
+      /* reading: under TRT the wall non-equilibrium, even in c at first order, decays
+       * with omega+ = 1/tau as under BGK */
       const double post = p->wall_neq_same ? 1.0 : (1.0 - omega);
       const double f0 = feq(&L, i, rF, u1) + fneq_ib;
       const double f1 = feq(&L, i, rF, u0) + post * fneq_ib;

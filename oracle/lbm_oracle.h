@@ -30,6 +30,9 @@ enum { OR_FLUID = 0, OR_SOLID = 1, OR_OPEN = 2 };
  * ELIBB unified linear / quadratic (Sec. II.E). */
 enum { OR_BC_ELIBB_F = 0, OR_BC_ELIBB_FQ = 1, OR_BC_BFL = 2, OR_BC_HWBB = 3,
        OR_BC_ELIBB_U = 4, OR_BC_ELIBB_UQ = 5 };
+/* Collision operators: single relaxation time (Eq. LB-BGK) and two relaxation
+ * times (Sec. II.A, TRT paragraph). */
+enum { OR_COLL_BGK = 0, OR_COLL_TRT = 1 };
 /* Analytic shapes for the link geometry. */
 enum { OR_SHAPE_SPHERE = 0,      /* solid inside |x-c| <= r0 (circle in 2D)        */
        OR_SHAPE_SPHERE_OUT = 1,  /* solid outside |x-c| >= r0                      */
@@ -51,6 +54,9 @@ typedef struct {
   int me_rho0;        /* 0: rho in the moving-wall term is rho_F(t) (default); 1: rho0 */
   int s1_exact;       /* 0: s of the post-collision wall population is 1 (default);
                          1: s = 1 + u_w.c_i/|c_i|^2 (Eq. x_to_s_helper as printed) */
+  int collision;      /* OR_COLL_BGK, or OR_COLL_TRT (two relaxation times, Sec. II.A) */
+  double magic;       /* TRT: Lambda = (1/omega+ - 1/2)(1/omega- - 1/2) (Eq. magic-parameter),
+                         omega+ = 1/tau */
 } or_params;
 
 typedef struct {
