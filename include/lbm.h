@@ -1,11 +1,11 @@
 /*
  * lbm.h -- C ABI of the GB300 (sm_103a) lattice Boltzmann library liblbm.so.
  *
- * The library advances the lattice Boltzmann equation with BGK collision on
- * D2Q9 and D3Q19 lattices (Sec. II.A, Eqs. LBE, LB-BGK, Eq2ndOrder of
- * arXiv:2009.04604) in one fused stream-collide kernel. On boundary nodes the same
- * kernel applies a link-wise curved-wall Dirichlet rule. The rules are ELIBB-F and
- * ELIBB-FQ (Sec. II.D), linear BFL (Sec. II.B, Eq. bfl) and half-way bounce-back,
+ * The library advances the lattice Boltzmann equation with BGK or TRT collision on
+ * D2Q9 and D3Q19 lattices (Sec. II.A, Eqs. LBE, LB-BGK, Eq2ndOrder, magic-parameter
+ * of arXiv:2009.04604) in one fused stream-collide kernel. On boundary nodes the
+ * same kernel applies a link-wise curved-wall Dirichlet rule. The rules are ELIBB-F,
+ * -FQ, -U and -UQ (Sec. II.D), linear BFL (Sec. II.B, Eq. bfl) and half-way bounce-back,
  * with the moving-wall term of Sec. II.E. Every rule takes its per-link wall
  * distance q and wall velocity u_w from the geometry. The momentum-exchange wall
  * force (Sec. II.F) and the total mass are reduced in FP64.
@@ -53,8 +53,16 @@ enum lbm_dtype { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2, LBM_BF16 = 3 };
  *            q < 0.01 (Sec. II.D, Eq. quadratic_fragmented_method);
  *   BFL      linear Bouzidi rule (Sec. II.B, Eq. bfl). It falls back to half-way
  *            bounce-back where the second fluid node along the link is missing;
- *   HWBB     half-way bounce-back (Sec. II.B). */
-enum lbm_bc { LBM_BC_ELIBB_F = 0, LBM_BC_ELIBB_FQ = 1, LBM_BC_BFL = 2, LBM_BC_HWBB = 3 };
+ *   HWBB     half-way bounce-back (Sec. II.B);
+ *   ELIBB_U  unified linear rule through the two wall populations
+ *            (Sec. II.D, Eq. unified_space_coordinates);
+ *   ELIBB_UQ unified quadratic rule (Sec. II.D, Eq. elibbqu), which falls back
+ *            to ELIBB_U for 1 - q < 0.01, where two of its points meet. */
+enum lbm_bc { LBM_BC_ELIBB_F = 0, LBM_BC_ELIBB_FQ = 1, LBM_BC_BFL = 2, LBM_BC_HWBB = 3,
+              LBM_BC_ELIBB_U = 4, LBM_BC_ELIBB_UQ = 5 };
+/* Collision operators: BGK (Sec. II.A, Eq. LB-BGK) and two relaxation times
+ * (Sec. II.A, TRT paragraph, Eq. magic-parameter). */
+enum lbm_collision { LBM_COLL_BGK = 0, LBM_COLL_TRT = 1 };
 
 /* Node kinds. A link into an OPEN node gets the single-node pressure rule
  * f_i = f_i^eq(rho0, u_F) + f^neq_ibar(x_F), the non-equilibrium bounce-back of
@@ -107,6 +115,17 @@ int lbm_destroy(lbm_handle h);
 /* Boundary rule (lbm_bc), reference density rho0 (default 1), constant body-force
  * density F (Guo forcing; NULL = none) and the x-wrap shear (0 = plain periodic). */
 int lbm_set_options(lbm_handle h, int bc, double rho0, const double force[3], int xshift);
+
+/* Collision operator (lbm_collision; BGK by default). Under TRT the even parts of
+ * the populations relax with omega+ = 1/tau and the odd parts with omega-, from
+ * the magic parameter Lambda = (1/omega+ - 1/2)(1/omega- - 1/2) (Eq.
+ * magic-parameter; the paper uses Lambda = 3/16, with which half-way bounce-back
+ * puts a flat wall exactly half-way at any tau). With Guo forcing, the even and
+ * odd parts of the source take the factors (1 - omega+/2) and (1 - omega-/2).
+ * The boundary rules use the TRT post-collision values; their post-collision
+ * wall estimate keeps the factor (1 - omega+). magic is ignored for BGK and must
+ * be positive for TRT; otherwise LBM_ERR_ARG. Takes effect at the next step. */
+int lbm_set_collision(lbm_handle h, int model, double magic);
 
 /* Explicit geometry from host arrays.
  *   flags[N]: lbm_node per node.

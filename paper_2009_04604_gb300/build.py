@@ -20,8 +20,13 @@ LIB = os.path.join(BUILD, "liblbm.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Multiply-add fusion happens in the front end only (explicit fma.rn in the PTX):
+# ptxas would otherwise fuse the remaining multiply/add pairs depending on each
+# kernel's register budget, and the same per-node code would round differently
+# in different kernels (a batched simulation against the same one stepped alone,
+# one launch variant against another).
 COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-                 "-I", INCLUDE]
+                 "-Xptxas", "--fmad=false", "-I", INCLUDE]
 # per-file extra flags: the geometry kernels round like the plain FP64 definitions
 EXTRA = {"geometry.cu": ["-fmad=false"]}
 # step_inst.cu: one object per (lattice, storage type)

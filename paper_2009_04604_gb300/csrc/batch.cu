@@ -1,9 +1,10 @@
 // batch.cu -- batched stepping of many independent simulations (lbm_batch_*).
 //
-// One launch per step advances every simulation of the batch. Its blocks run
-// the tiles of all simulations, one simulation after another, each one's table
-// plane-interleaved as in the single-simulation step. The steps replay from
-// captured CUDA graphs.
+// One launch per step and physics class (body force on or off, BGK or TRT; a
+// batch of like simulations has one class) advances every simulation of the
+// batch. Its blocks run the tiles of the class's simulations, one simulation
+// after another, each one's table plane-interleaved as in the single-simulation
+// step. The steps replay from captured CUDA graphs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,6 +26,7 @@ struct lbm_batch_s {
   BatchEntry *entries = nullptr;
   int4 *tiles = nullptr;
   long long ntiles = 0;
+  long long cls_first[4] = {0, 0, 0, 0}, cls_count[4] = {0, 0, 0, 0};  // tile range per physics class
   int bx = 32, by = 4, variant = 3, T = 1;
   bool tiles_ok = false;
   int parity = 0;  // batch steps taken since the entries were built, mod 2
@@ -47,12 +49,24 @@ static int bfail(lbm_batch b, int code, const std::string &msg) {
                    std::string(#call) + ": " + cudaGetErrorString(e_));                          \
   } while (0)
 
+template <class L, typename S, typename M, int MINB, int PHYS>
+static cudaError_t batch_class(const lbm_batch_s *b, int parity) {
+  const long long n = b->cls_count[PHYS];
+  if (n == 0) return cudaSuccess;
+  const dim3 block(b->bx, b->by, 1);
+  const unsigned grid = (unsigned)((n + b->T - 1) / b->T);
+  k_step_batch<L, S, M, MINB, PHYS><<<grid, block, 0, b->stream>>>(b->entries, b->tiles + b->cls_first[PHYS],
+                                                                    (int)n, b->T, parity);
+  return cudaGetLastError();
+}
+
 template <class L, typename S, typename M, int MINB>
 static cudaError_t batch_variant(const lbm_batch_s *b, int parity) {
-  const dim3 block(b->bx, b->by, 1);
-  const unsigned grid = (unsigned)((b->ntiles + b->T - 1) / b->T);
-  k_step_batch<L, S, M, MINB><<<grid, block, 0, b->stream>>>(b->entries, b->tiles, (int)b->ntiles, b->T, parity);
-  return cudaGetLastError();
+  cudaError_t e = batch_class<L, S, M, MINB, 0>(b, parity);
+  if (e == cudaSuccess) e = batch_class<L, S, M, MINB, PH_FORCE>(b, parity);
+  if (e == cudaSuccess) e = batch_class<L, S, M, MINB, PH_TRT>(b, parity);
+  if (e == cudaSuccess) e = batch_class<L, S, M, MINB, PH_FORCE | PH_TRT>(b, parity);
+  return e;
 }
 
 template <class L, typename S, typename M>
@@ -100,8 +114,19 @@ static int build_batch(lbm_batch b) {
   b->base_cur.resize(n);
   b->base_ver.resize(n);
   const int tpb = b->bx * b->by;
-  for (int k = 0; k < n; ++k) {
+  // simulations by physics class, in batch order within a class
+  std::vector<int> order;
+  for (int c = 0; c < 4; ++c)
+    for (int k = 0; k < n; ++k) {
+      const lbm_sim *s = b->sims[k];
+      if (((s->has_force ? PH_FORCE : 0) | (s->collision == LBM_COLL_TRT ? PH_TRT : 0)) == c) order.push_back(k);
+    }
+  for (int c = 0; c < 4; ++c) b->cls_count[c] = 0;
+  for (int k : order) {
     lbm_sim *s = b->sims[k];
+    const int c = (s->has_force ? PH_FORCE : 0) | (s->collision == LBM_COLL_TRT ? PH_TRT : 0);
+    if (b->cls_count[c] == 0) b->cls_first[c] = (long long)t.size();
+    const size_t t0 = t.size();
     const int save_bx = s->step_bx;
     s->step_bx = b->bx;  // the view's tile-row count follows the batch's block width
     e[k].v = s->view();
@@ -125,6 +150,7 @@ static int build_batch(lbm_batch b) {
       for (long long r = r0; r < r1; r += tpb)
         t.push_back(make_int4(k, -1, (int)r, (int)std::min<long long>(tpb, r1 - r)));
     }
+    b->cls_count[c] += (long long)(t.size() - t0);
   }
   drop_batch_graphs(b);
   cudaFree(b->entries);

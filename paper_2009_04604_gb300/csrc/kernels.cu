@@ -51,10 +51,10 @@ static cudaError_t dispatch(int lattice, int dtype, Fn &&fn) {
 
 LBM_STEP_INSTANCES(LBM_STEP_DECLARE)
 
-cudaError_t prepare_step_tma(int lattice, int dtype, int has_force, int bx, int by, long long ntiles,
+cudaError_t prepare_step_tma(int lattice, int dtype, int phys, int bx, int by, long long ntiles,
                              int *blocks, int *smem) {
   return dispatch(lattice, dtype, [&]<class L, typename S, typename M>() {
-    return prepare_step_tma_ls<L, S>(has_force, bx, by, ntiles, blocks, smem);
+    return prepare_step_tma_ls<L, S>(phys, bx, by, ntiles, blocks, smem);
   });
 }
 

@@ -29,7 +29,7 @@
 
 namespace lbm {
 
-enum { BC_ELIBB_F = 0, BC_ELIBB_FQ = 1, BC_BFL = 2, BC_HWBB = 3 };
+enum { BC_ELIBB_F = 0, BC_ELIBB_FQ = 1, BC_BFL = 2, BC_HWBB = 3, BC_ELIBB_U = 4, BC_ELIBB_UQ = 5 };
 
 // ---------------------------------------------------------------- gather
 template <class L, typename S, typename M>
@@ -123,78 +123,97 @@ __device__ __forceinline__ M feq_s(int i, M drho, M rho, M ux, M uy, M uz, M usq
   return M(weight<L>(i)) * (drho + rho * (M(3) * cu + M(4.5) * cu * cu - M(1.5) * usq));
 }
 
-// Guo source (1 - omega/2) w_i [3 (c_i - u).F + 9 (c_i.u)(c_i.F)]
-template <class L, typename M>
-__device__ __forceinline__ M guo(const View &v, int i, const Macro<L, M> &m) {
-  const Par<M> P(v);
-  const M Fx = P.F[0], Fy = P.F[1], Fz = P.F[2];
-  const M cu = M(L::cx(i)) * m.ux + M(L::cy(i)) * m.uy + M(L::cz(i)) * m.uz;
-  const M cF = M(L::cx(i)) * Fx + M(L::cy(i)) * Fy + M(L::cz(i)) * Fz;
-  const M uF = m.ux * Fx + m.uy * Fy + m.uz * Fz;
-  return (M(1) - M(0.5) * P.omega) * M(weight<L>(i)) * (M(3) * (cF - uF) + M(9) * cu * cF);
-}
+// Compile-time physics of a step kernel: bit 0 adds the Guo body force, bit 1
+// selects the TRT collision instead of BGK.
+enum : int { PH_FORCE = 1, PH_TRT = 2 };
 
-// post-collision shifted population f*_i = f_i + omega (f^eq_i - f_i) + S_i
-template <class L, typename M>
-__device__ __forceinline__ M post(const View &v, int i, const M fi, const Macro<L, M> &m) {
-  M r = fi + Par<M>(v).omega * (feq_s<L, M>(i, m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - fi);
-  if (v.has_force) r += guo<L, M>(v, i, m);
-  return r;
-}
-
-// Bulk BGK relaxation and store, by opposite pairs (i, ibar). With
-// omega f^eq_i = w [omega (drho - 3/2 rho u^2) + 9/2 omega rho (c.u)^2] + 3 w omega rho (c.u),
-// the even part is shared by the pair and the odd part flips sign, and
-// f*_i = (1 - omega) f_i + omega f^eq_i + S_i. The Guo source splits the same way:
-// S = k w (9 (c.u)(c.F) - 3 u.F) + 3 k w (c.F), with k = 1 - omega/2.
+// Bulk relaxation, by opposite pairs (i, ibar). The shifted equilibrium splits into
+// an even part e+ = w [drho - 3/2 rho u^2 + 9/2 rho (c.u)^2], shared by the pair,
+// and an odd part e- = 3 w rho (c.u), which flips sign. The Guo source splits the
+// same way: S+ = w (9 (c.u)(c.F) - 3 u.F), S- = 3 w (c.F).
+//  - BGK (Eq. LB-BGK): f*_i = (1 - omega) f_i + omega (e+ + e-) + k (S+ + S-),
+//    k = 1 - omega/2.
+//  - TRT (Sec. II.A): with f+ = (f_i + f_ibar)/2 and f- = (f_i - f_ibar)/2,
+//    f*_i = f_i + omega+ (e+ - f+) + omega- (e- - f-) + k+ S+ + k- S-, where
+//    k+- = 1 - omega+-/2, omega+ = 1/tau and omega- follows from the magic
+//    parameter (Eq. magic-parameter).
 // The relaxed value of direction i goes to put(i, value); collide_store writes it
 // to the output planes, post_all to registers.
-template <class L, typename M, bool FORCE, class Put>
+template <class L, typename M, int PHYS, class Put>
 __device__ __forceinline__ void relax(const View &v, const M (&f)[L::Q], const Macro<L, M> &m, Put &&put) {
+  constexpr bool FORCE = (PHYS & PH_FORCE) != 0, TRT = (PHYS & PH_TRT) != 0;
   constexpr int R = L::Q / 2;
   const Par<M> P(v);
   const M om = P.omega, omr = M(1) - om;
-  const M wr = om * m.rho;
-  const M b0 = om * (m.drho - M(1.5) * m.rho * m.usq);
-  M Fx = M(0), Fy = M(0), Fz = M(0), kf = M(0), uF = M(0);
+  M Fx = M(0), Fy = M(0), Fz = M(0), kf = M(0), km = M(0), uF = M(0);
   if constexpr (FORCE) {
     Fx = P.F[0]; Fy = P.F[1]; Fz = P.F[2];
     kf = M(1) - M(0.5) * om;
+    if constexpr (TRT) km = M(1) - M(0.5) * P.omega_m;
     uF = m.ux * Fx + m.uy * Fy + m.uz * Fz;
   }
-  {
-    const M w = M(weight<L>(R));
-    M eq = w * b0;
-    if constexpr (FORCE) eq -= M(3) * kf * w * uF;
-    put(R, omr * f[R] + eq);
-  }
-#pragma unroll
-  for (int i = 0; i < R; ++i) {
-    const int j = L::Q - 1 - i;
-    const M w = M(weight<L>(i));
-    const M cu = M(L::cx(i)) * m.ux + M(L::cy(i)) * m.uy + M(L::cz(i)) * m.uz;
-    M sym = w * (b0 + M(4.5) * wr * cu * cu);
-    M asym = M(3) * w * wr * cu;
-    if constexpr (FORCE) {
-      const M cF = M(L::cx(i)) * Fx + M(L::cy(i)) * Fy + M(L::cz(i)) * Fz;
-      sym += kf * w * (M(9) * cu * cF - M(3) * uF);
-      asym += M(3) * kf * w * cF;
+  if constexpr (TRT) {
+    const M omm = P.omega_m;
+    const M d0 = m.drho - M(1.5) * m.rho * m.usq;
+    {
+      const M w = M(weight<L>(R));
+      M r = f[R] + om * (w * d0 - f[R]);
+      if constexpr (FORCE) r -= M(3) * kf * w * uF;
+      put(R, r);
     }
-    put(i, omr * f[i] + (sym + asym));
-    put(j, omr * f[j] + (sym - asym));
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int j = L::Q - 1 - i;
+      const M w = M(weight<L>(i));
+      const M cu = M(L::cx(i)) * m.ux + M(L::cy(i)) * m.uy + M(L::cz(i)) * m.uz;
+      const M ep = w * (d0 + M(4.5) * m.rho * cu * cu), em = M(3) * w * m.rho * cu;
+      M dp = om * (ep - M(0.5) * (f[i] + f[j]));
+      M dm = omm * (em - M(0.5) * (f[i] - f[j]));
+      if constexpr (FORCE) {
+        const M cF = M(L::cx(i)) * Fx + M(L::cy(i)) * Fy + M(L::cz(i)) * Fz;
+        dp += kf * w * (M(9) * cu * cF - M(3) * uF);
+        dm += M(3) * km * w * cF;
+      }
+      put(i, f[i] + (dp + dm));
+      put(j, f[j] + (dp - dm));
+    }
+  } else {
+    const M wr = om * m.rho;
+    const M b0 = om * (m.drho - M(1.5) * m.rho * m.usq);
+    {
+      const M w = M(weight<L>(R));
+      M eq = w * b0;
+      if constexpr (FORCE) eq -= M(3) * kf * w * uF;
+      put(R, omr * f[R] + eq);
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int j = L::Q - 1 - i;
+      const M w = M(weight<L>(i));
+      const M cu = M(L::cx(i)) * m.ux + M(L::cy(i)) * m.uy + M(L::cz(i)) * m.uz;
+      M sym = w * (b0 + M(4.5) * wr * cu * cu);
+      M asym = M(3) * w * wr * cu;
+      if constexpr (FORCE) {
+        const M cF = M(L::cx(i)) * Fx + M(L::cy(i)) * Fy + M(L::cz(i)) * Fz;
+        sym += kf * w * (M(9) * cu * cF - M(3) * uF);
+        asym += M(3) * kf * w * cF;
+      }
+      put(i, omr * f[i] + (sym + asym));
+      put(j, omr * f[j] + (sym - asym));
+    }
   }
 }
 
-template <class L, typename S, typename M, bool FORCE>
+template <class L, typename S, typename M, int PHYS>
 __device__ __forceinline__ void collide_store(const View &v, const M (&f)[L::Q], const Macro<L, M> &m,
                                               S *__restrict__ dst, int np) {
-  relax<L, M, FORCE>(v, f, m, [&](int i, M val) { dst[i * np] = to_store<S, M>(val); });
+  relax<L, M, PHYS>(v, f, m, [&](int i, M val) { dst[i * np] = to_store<S, M>(val); });
 }
 
-template <class L, typename M, bool FORCE>
+template <class L, typename M, int PHYS>
 __device__ __forceinline__ void post_all(const View &v, const M (&f)[L::Q], const Macro<L, M> &m,
                                          M (&out)[L::Q]) {
-  relax<L, M, FORCE>(v, f, m, [&](int i, M val) { out[i] = val; });
+  relax<L, M, PHYS>(v, f, m, [&](int i, M val) { out[i] = val; });
 }
 
 // ---------------------------------------------------------------- boundary rule
@@ -204,29 +223,81 @@ __device__ __forceinline__ void post_all(const View &v, const M (&f)[L::Q], cons
 //   g  = f*_ibar(x_F) + ME, ME = 2 w_i rho_F c_i.u_w / c_s^2 (Eq. ME-solid-to-fluid)  s = 1-q
 //   f1 = f~*_i(x_W) = f^eq_i(rho_F, u_w(t)) + (1 - omega) f^neq_ibar(x_F)          s = 1
 //   h  = f*_i(x_F)                                                                 s = 1+q
-// Weights: Lagrange weights (Eq. poli_coeff) at s_ref = q, in closed form. At
-// q = 1/2 every rule reduces exactly to g (half-way bounce-back).
+// Weights: Lagrange weights (Eq. poli_coeff) at s_ref = q, in closed form:
+//   ELIBB-F  (Eq. linear_broken_method): f0, g for q < 1/2; g, f1 for q >= 1/2;
+//   ELIBB-FQ (Eq. quadratic_fragmented_method): f0, g, f1 for q < 1/2 (ELIBB-F
+//            below q_cut); g, f1, h for q >= 1/2;
+//   ELIBB-U  (Eq. unified_space_coordinates): (1 - q) f0 + q f1;
+//   ELIBB-UQ (Eq. elibbqu): f0, g, f1 for every q, which is
+//            (1 - 2q) f0 + g + (2q - 1) f1; ELIBB-U where 1 - q < q_cut, where
+//            the points s = 0 and s = 1 - q meet.
+// At q = 1/2 every rule but ELIBB-U reduces exactly to g (half-way bounce-back).
+// Under TRT the post-collision wall value f1 keeps the factor (1 - omega+): the
+// wall non-equilibrium is even in c at first order.
 // The loop runs over the set bits of the link masks with a run-time direction
 // index, which keeps the code small. The node's populations sit in shared memory
 // (fs[i*stride]), and the direction constants come from packed words.
 
-// shifted equilibrium for a run-time direction
+// The rule is written with explicitly rounded operations (Ex<M>: one rounding
+// per multiply, add and fused multiply-add, in the order written). The compiler
+// is then free neither to fuse nor to split them, so every kernel that inlines
+// the rule (the step variants, the batched step) rounds exactly alike.
+template <typename M> struct Ex;
+template <> struct Ex<float> {
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+};
+template <> struct Ex<double> {
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+  static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+};
+
+// c_i . a for a run-time direction
 template <class L, typename M>
-__device__ __forceinline__ M feq_r(int i, M drho, M rho, M ux, M uy, M uz, M usq) {
-  const M cu = M(dcx<L>(i)) * ux + M(dcy<L>(i)) * uy + M(dcz<L>(i)) * uz;
-  return dweight<L, M>(i) * (drho + rho * (M(3) * cu + M(4.5) * cu * cu - M(1.5) * usq));
+__device__ __forceinline__ M cdot_r(int i, M ax, M ay, M az) {
+  using X = Ex<M>;
+  return X::fma(M(dcz<L>(i)), az, X::fma(M(dcy<L>(i)), ay, X::mul(M(dcx<L>(i)), ax)));
 }
 
-// post-collision (with Guo source) for a run-time direction
+// shifted equilibrium w_i [drho + rho (3 cu + 9/2 cu^2 - 3/2 u^2)] for a run-time direction
 template <class L, typename M>
-__device__ __forceinline__ M post_r(const View &v, const Par<M> &P, int i, M fi, const Macro<L, M> &m) {
-  M r = fi + P.omega * (feq_r<L, M>(i, m.drho, m.rho, m.ux, m.uy, m.uz, m.usq) - fi);
+__device__ __forceinline__ M feq_r(int i, M drho, M rho, M ux, M uy, M uz, M usq) {
+  using X = Ex<M>;
+  const M cu = cdot_r<L, M>(i, ux, uy, uz);
+  const M t = X::fma(X::mul(M(4.5), cu), cu, X::fma(M(3), cu, X::mul(M(-1.5), usq)));
+  return X::mul(dweight<L, M>(i), X::fma(rho, t, drho));
+}
+
+// post-collision value (with the Guo source) of direction i, whose opposite
+// population is fo, for a run-time direction; BGK or TRT as in relax
+template <class L, typename M>
+__device__ __forceinline__ M post_r(const View &v, const Par<M> &P, int i, M fi, M fo, const Macro<L, M> &m) {
+  using X = Ex<M>;
+  const M w = dweight<L, M>(i);
+  const M cu = cdot_r<L, M>(i, m.ux, m.uy, m.uz);
+  M r;
+  if (v.trt) {
+    const M e2 = X::fma(X::mul(M(4.5), cu), cu, X::mul(M(-1.5), m.usq));
+    const M ep = X::mul(w, X::fma(m.rho, e2, m.drho));
+    const M em = X::mul(X::mul(M(3), w), X::mul(m.rho, cu));
+    const M fp = X::mul(M(0.5), X::add(fi, fo)), fm = X::mul(M(0.5), X::sub(fi, fo));
+    r = X::fma(P.omega_m, X::sub(em, fm), X::fma(P.omega, X::sub(ep, fp), fi));
+  } else {
+    r = X::fma(P.omega, X::sub(feq_r<L, M>(i, m.drho, m.rho, m.ux, m.uy, m.uz, m.usq), fi), fi);
+  }
   if (v.has_force) {
-    const M cx = M(dcx<L>(i)), cy = M(dcy<L>(i)), cz = M(dcz<L>(i));
-    const M cu = cx * m.ux + cy * m.uy + cz * m.uz;
-    const M cF = cx * P.F[0] + cy * P.F[1] + cz * P.F[2];
-    const M uF = m.ux * P.F[0] + m.uy * P.F[1] + m.uz * P.F[2];
-    r += (M(1) - M(0.5) * P.omega) * dweight<L, M>(i) * (M(3) * (cF - uF) + M(9) * cu * cF);
+    const M cF = cdot_r<L, M>(i, P.F[0], P.F[1], P.F[2]);
+    const M uF = X::fma(m.uz, P.F[2], X::fma(m.uy, P.F[1], X::mul(m.ux, P.F[0])));
+    const M kp = X::fma(M(-0.5), P.omega, M(1));
+    const M km = X::fma(M(-0.5), v.trt ? P.omega_m : P.omega, M(1));
+    const M sp = X::fma(X::mul(M(9), cu), cF, X::mul(M(-3), uF));
+    r = X::fma(w, X::fma(kp, sp, X::mul(X::mul(M(3), km), cF)), r);
   }
   return r;
 }
@@ -245,6 +316,7 @@ __device__ __forceinline__ int upstream_offset(const View &v, int x, int y, int 
 template <class L, typename S, typename M>
 __device__ void boundary(const View &v, const RecSet &rs, const Rec &r, const M *fs, int stride,
                          const Macro<L, M> &m, long long n, int x, int y, int z, S *__restrict__ fout) {
+  using X = Ex<M>;
   const M *lq = static_cast<const M *>(rs.lq);
   const M *luw = static_cast<const M *>(rs.luw);
   const M *luw1 = static_cast<const M *>(rs.luw1);
@@ -258,13 +330,12 @@ __device__ void boundary(const View &v, const RecSet &rs, const Rec &r, const M 
     const uint32_t bit = 1u << i;
     links &= links - 1u;
     const int ib = opp<L>(i);
-    const int cx = dcx<L>(i), cy = dcy<L>(i), cz = dcz<L>(i);
     const M fib = fs[ib * stride];
     M val;
     if (open & bit) {
       // single-node pressure outlet: f^eq_i(rho0, u_F) + f^neq_ibar(x_F)
-      const M fneq_ib = fib - feq_r<L, M>(ib, m.drho, m.rho, m.ux, m.uy, m.uz, m.usq);
-      val = feq_r<L, M>(i, M(0), P.rho0, m.ux, m.uy, m.uz, m.usq) + fneq_ib;
+      const M fneq_ib = X::sub(fib, feq_r<L, M>(ib, m.drho, m.rho, m.ux, m.uy, m.uz, m.usq));
+      val = X::add(feq_r<L, M>(i, M(0), P.rho0, m.ux, m.uy, m.uz, m.usq), fneq_ib);
     } else {
       const uint32_t li = r.link0 + __popc(r.cut & (bit - 1u));
       const M q = lq[li];
@@ -274,41 +345,47 @@ __device__ void boundary(const View &v, const RecSet &rs, const Rec &r, const M 
         vx = luw1[3 * li]; vy = luw1[3 * li + 1]; vz = luw1[3 * li + 2];
       }
       const M w = dweight<L, M>(i);
-      const M cu0 = M(cx) * wx + M(cy) * wy + M(cz) * wz;
-      const M me = M(6) * w * m.rho * cu0;
-      const M g = post_r<L, M>(v, P, ib, fib, m) + me;
-      if (v.bc == BC_HWBB || q == M(0.5)) {
+      const M me = X::mul(X::mul(X::mul(M(6), w), m.rho), cdot_r<L, M>(i, wx, wy, wz));
+      const M fi = fs[i * stride];
+      const M g = X::add(post_r<L, M>(v, P, ib, fib, fi, m), me);
+      const M q2 = X::mul(M(2), q);               // 2q (exact)
+      const M a = X::sub(q2, M(1)), oma = X::sub(M(1), q2);  // 2q - 1, 1 - 2q
+      const M omq = X::sub(M(1), q);              // 1 - q
+      if (v.bc == BC_HWBB || (q == M(0.5) && v.bc != BC_ELIBB_U)) {
         val = g;
       } else if (v.bc == BC_BFL) {
         if (q < M(0.5)) {
-          val = (r.ffok & bit) ? M(2) * q * g + (M(1) - M(2) * q) * me : g;
+          val = (r.ffok & bit) ? X::fma(q2, g, X::mul(oma, me)) : g;
         } else {
-          const M h = post_r<L, M>(v, P, i, fs[i * stride], m);
-          val = (g + (M(2) * q - M(1)) * h) / (M(2) * q);
+          const M h = post_r<L, M>(v, P, i, fi, fib, m);
+          val = X::div(X::fma(a, h, g), q2);
         }
       } else {
-        const M fneq_ib = fib - feq_r<L, M>(ib, m.drho, m.rho, m.ux, m.uy, m.uz, m.usq);
-        const M u0sq = wx * wx + wy * wy + wz * wz;
-        const M f1 = feq_r<L, M>(i, m.drho, m.rho, wx, wy, wz, u0sq) + (M(1) - P.omega) * fneq_ib;
-        if (q < M(0.5)) {
-          const M u1sq = vx * vx + vy * vy + vz * vz;
-          const M f0 = feq_r<L, M>(i, m.drho, m.rho, vx, vy, vz, u1sq) + fneq_ib;
-          if (v.bc == BC_ELIBB_FQ && q >= P.qcut)
-            val = (M(1) - M(2) * q) * f0 + g + (M(2) * q - M(1)) * f1;
+        const M fneq_ib = X::sub(fib, feq_r<L, M>(ib, m.drho, m.rho, m.ux, m.uy, m.uz, m.usq));
+        const M u0sq = X::fma(wz, wz, X::fma(wy, wy, X::mul(wx, wx)));
+        const M f1 = X::fma(X::sub(M(1), P.omega), fneq_ib, feq_r<L, M>(i, m.drho, m.rho, wx, wy, wz, u0sq));
+        const bool unified_lin = v.bc == BC_ELIBB_U || (v.bc == BC_ELIBB_UQ && omq < P.qcut);
+        if (unified_lin || q < M(0.5) || v.bc == BC_ELIBB_UQ) {
+          const M u1sq = X::fma(vz, vz, X::fma(vy, vy, X::mul(vx, vx)));
+          const M f0 = X::add(feq_r<L, M>(i, m.drho, m.rho, vx, vy, vz, u1sq), fneq_ib);
+          if (unified_lin)  // ELIBB-U: the wall points s = 0 and s = 1 only
+            val = X::fma(q, f1, X::mul(omq, f0));
+          else if ((v.bc == BC_ELIBB_FQ && q >= P.qcut) || v.bc == BC_ELIBB_UQ)
+            val = X::fma(a, f1, X::fma(oma, f0, g));                  // (1-2q) f0 + g + (2q-1) f1
           else
-            val = ((M(1) - M(2) * q) * f0 + q * g) / (M(1) - q);
+            val = X::div(X::fma(q, g, X::mul(oma, f0)), omq);         // ((1-2q) f0 + q g) / (1-q)
+        } else if (v.bc == BC_ELIBB_FQ) {
+          // ((1-q) g + 2 (2q-1) f1 + (2q-1)(q-1) h) / (2 q^2)
+          const M h = post_r<L, M>(v, P, i, fi, fib, m);
+          val = X::div(X::fma(X::mul(a, X::sub(q, M(1))), h, X::fma(X::mul(M(2), a), f1, X::mul(omq, g))),
+                       X::mul(q2, q));
         } else {
-          if (v.bc == BC_ELIBB_FQ) {
-            const M h = post_r<L, M>(v, P, i, fs[i * stride], m);
-            const M a = M(2) * q - M(1);
-            val = ((M(1) - q) * g + M(2) * a * f1 + a * (q - M(1)) * h) / (M(2) * q * q);
-          } else {
-            val = ((M(1) - q) * g + (M(2) * q - M(1)) * f1) / q;
-          }
+          val = X::div(X::fma(a, f1, X::mul(omq, g)), q);              // ((1-q) g + (2q-1) f1) / q
         }
       }
     }
-    fout[(long long)i * v.np + n + upstream_offset(v, x, y, z, cx, cy, cz)] = to_store<S, M>(val);
+    fout[(long long)i * v.np + n + upstream_offset(v, x, y, z, dcx<L>(i), dcy<L>(i), dcz<L>(i))] =
+        to_store<S, M>(val);
   }
 }
 
@@ -368,10 +445,11 @@ __device__ __forceinline__ void boundary_node(const View &v, const RecSet &rs, c
 // warps, where wall rows would otherwise diverge into it for every lane.
 // MINB is the minimum number of resident 256-thread blocks per SM that the
 // register allocation must allow (1: unconstrained); the autotuner picks it.
-// FORCE selects the body-force path at compile time. Element offsets are 32-bit,
+// PHYS selects the body-force path and the collision (PH_FORCE, PH_TRT) at
+// compile time. Element offsets are 32-bit,
 // since the library keeps Q x padded nodes below 2^31 per simulation.
 // Lattice tile {z, t} of the table: gather, relax and store every fluid node.
-template <class L, typename S, typename M, bool FORCE>
+template <class L, typename S, typename M, int PHYS>
 __device__ __forceinline__ void lattice_tile(const View &v, const S *__restrict__ fin,
                                              S *__restrict__ fout, int2 tile) {
   const int x = (tile.y % v.gx) * blockDim.x + threadIdx.x;
@@ -406,7 +484,7 @@ __device__ __forceinline__ void lattice_tile(const View &v, const S *__restrict_
   }
   if (v.bc == BC_BFL && (fl & F_BOUNDARY)) bfl_complete<L, M>(v, *record_of(v, n, bal), f);
   const Macro<L, M> m = moments<L, M>(v, f);
-  collide_store<L, S, M, FORCE>(v, f, m, fout + n, np);
+  collide_store<L, S, M, PHYS>(v, f, m, fout + n, np);
 }
 
 // ---------------------------------------------------------------- two nodes per thread
@@ -442,7 +520,7 @@ template <> struct Vec2<__nv_bfloat16> {
   __device__ static T make(float a, float b) { return __floats2bfloat162_rn(a, b); }
 };
 
-template <class L, typename S, typename M, bool FORCE>
+template <class L, typename S, typename M, int PHYS>
 __device__ __forceinline__ void lattice_tile_pair(const View &v, const S *__restrict__ fin,
                                                   S *__restrict__ fout, int2 tile) {
   using V = Vec2<S>;
@@ -512,8 +590,8 @@ __device__ __forceinline__ void lattice_tile_pair(const View &v, const S *__rest
   // that only the stores of pairs with a non-fluid node diverge
   const Macro<L, M> ma = moments<L, M>(v, f0), mb = moments<L, M>(v, f1);
   M pa[L::Q], pb[L::Q];
-  post_all<L, M, FORCE>(v, f0, ma, pa);
-  post_all<L, M, FORCE>(v, f1, mb, pb);
+  post_all<L, M, PHYS>(v, f0, ma, pa);
+  post_all<L, M, PHYS>(v, f1, mb, pb);
   if (fa && fb) {
 #pragma unroll
     for (int i = 0; i < L::Q; ++i)
@@ -552,7 +630,7 @@ __device__ __forceinline__ void boundary_tile(const View &v, const S *__restrict
 
 // Block b takes table entries b*T .. b*T+T-1 (T = v.tpb_tiles <= 4), whose
 // descriptors it loads together up front.
-template <class L, typename S, typename M, int MINB, bool FORCE, bool PAIR = false>
+template <class L, typename S, typename M, int MINB, int PHYS, bool PAIR = false>
 __global__ void __launch_bounds__(256, MINB) k_step(const View v, const S *__restrict__ fin,
                                                     S *__restrict__ fout) {
   __shared__ M stage[L::Q * 256];  // boundary tiles: populations, [direction][thread]
@@ -566,8 +644,8 @@ __global__ void __launch_bounds__(256, MINB) k_step(const View v, const S *__res
   for (int k = 0; k < 4; ++k) {
     if (k >= T || first + k >= v.ntiles) break;
     if (tl[k].x < 0) boundary_tile<L, S, M>(v, fin, fout, tl[k], stage);
-    else if constexpr (PAIR) lattice_tile_pair<L, S, M, FORCE>(v, fin, fout, tl[k]);
-    else lattice_tile<L, S, M, FORCE>(v, fin, fout, tl[k]);
+    else if constexpr (PAIR) lattice_tile_pair<L, S, M, PHYS>(v, fin, fout, tl[k]);
+    else lattice_tile<L, S, M, PHYS>(v, fin, fout, tl[k]);
   }
 }
 
@@ -672,7 +750,7 @@ __device__ void tma_issue(const View &v, const S *__restrict__ fin, int2 tile, u
 }
 
 // Consumer: one node per thread from the stage.
-template <class L, typename S, typename M, bool FORCE>
+template <class L, typename S, typename M, int PHYS>
 __device__ __forceinline__ void tma_lattice(const View &v, const S *__restrict__ fin, S *__restrict__ fout,
                                             int2 tile, const unsigned char *base, const TmaLayout<S> &lay) {
   constexpr int HALO = TmaLayout<S>::HALO;
@@ -705,10 +783,10 @@ __device__ __forceinline__ void tma_lattice(const View &v, const S *__restrict__
   }
   if (v.bc == BC_BFL && (fl & F_BOUNDARY)) bfl_complete<L, M>(v, *record_of(v, n, bal), f);
   const Macro<L, M> m = moments<L, M>(v, f);
-  collide_store<L, S, M, FORCE>(v, f, m, fout + n, np);
+  collide_store<L, S, M, PHYS>(v, f, m, fout + n, np);
 }
 
-template <class L, typename S, typename M, bool FORCE>
+template <class L, typename S, typename M, int PHYS>
 __global__ void __launch_bounds__(256, 2) k_step_tma(const View v, const S *__restrict__ fin,
                                                      S *__restrict__ fout, int nstage, int stage_bytes) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -758,7 +836,7 @@ __global__ void __launch_bounds__(256, 2) k_step_tma(const View v, const S *__re
         return;
       }
       parity ^= 1u << k;
-      tma_lattice<L, S, M, FORCE>(v, fin, fout, tile, stages + k * stage_bytes, lay);
+      tma_lattice<L, S, M, PHYS>(v, fin, fout, tile, stages + k * stage_bytes, lay);
     }
     __syncthreads();  // the stage is free for the producer
   }
@@ -770,16 +848,17 @@ __global__ void __launch_bounds__(256, 2) k_step_tma(const View v, const S *__re
 // {sim, z, t, 0} lattice tiles and {sim, -1, first, count} boundary tiles, one
 // simulation after another, each plane-interleaved as in k_step. parity picks
 // which buffer of each entry is read in this step. A block copies the entry of
-// its tile into shared memory. The per-node code is the same as k_step's,
-// including the per-simulation choice of the force path. A batched simulation
-// therefore gives exactly the results it gives when stepped alone.
+// its tile into shared memory. The table is grouped by physics class (body
+// force, collision operator), and one launch covers one class, compiled for it
+// (PHYS) as k_step is. The per-node code is the same as k_step's, so a batched
+// simulation gives exactly the results it gives when stepped alone.
 struct BatchEntry {
   View v;
   const void *f0;  // read on even batch steps
   void *f1;        // read on odd batch steps
 };
 
-template <class L, typename S, typename M, int MINB>
+template <class L, typename S, typename M, int MINB, int PHYS>
 __global__ void __launch_bounds__(256, MINB) k_step_batch(const BatchEntry *__restrict__ entries,
                                                           const int4 *__restrict__ tiles, int ntiles,
                                                           int T, int parity) {
@@ -795,10 +874,10 @@ __global__ void __launch_bounds__(256, MINB) k_step_batch(const BatchEntry *__re
     __syncthreads();
     const S *fin = static_cast<const S *>(parity ? se.f1 : se.f0);
     S *fout = static_cast<S *>(parity ? const_cast<void *>(se.f0) : se.f1);
-    // each simulation takes the same compiled path as when it steps alone
+    // each simulation takes the same compiled path as when it steps alone: the
+    // launch covers the simulations of one physics class (PHYS) only
     if (tile.y < 0) boundary_tile<L, S, M>(se.v, fin, fout, make_int2(-1 - tile.w, tile.z), stage);
-    else if (se.v.has_force) lattice_tile<L, S, M, true>(se.v, fin, fout, make_int2(tile.y, tile.z));
-    else lattice_tile<L, S, M, false>(se.v, fin, fout, make_int2(tile.y, tile.z));
+    else lattice_tile<L, S, M, PHYS>(se.v, fin, fout, make_int2(tile.y, tile.z));
   }
 }
 

@@ -130,9 +130,11 @@ struct View {
   double omega, rho0, qcut;  // 1/tau, reference density, ELIBB-FQ cutoff
   double F[3];               // body-force density
   int has_force, has_uw;
+  int trt;                   // 1: TRT collision, odd parts relax with omega_m
+  double omega_m;            // TRT omega- (Eq. magic-parameter); equals omega under BGK
   // the same scalars in FP32, so that FP32 kernels convert nothing on the
-  // (slow) FP64 pipe: omega, rho0, qcut, F
-  float omega_f, rho0_f, qcut_f, F_f[3];
+  // (slow) FP64 pipe: omega, rho0, qcut, F, omega_m
+  float omega_f, rho0_f, qcut_f, F_f[3], omega_m_f;
   const uint8_t *flags;      // [np]
   const uint32_t *cbase;     // [np/32] records before each 32-node chunk
   const Rec *rec;            // [nb]
@@ -155,14 +157,15 @@ struct View {
 // Scalar parameters in the math type of a kernel.
 template <typename M> struct Par;
 template <> struct Par<double> {
-  double omega, rho0, qcut, F[3];
+  double omega, rho0, qcut, F[3], omega_m;
   __device__ __forceinline__ explicit Par(const View &v)
-      : omega(v.omega), rho0(v.rho0), qcut(v.qcut), F{v.F[0], v.F[1], v.F[2]} {}
+      : omega(v.omega), rho0(v.rho0), qcut(v.qcut), F{v.F[0], v.F[1], v.F[2]}, omega_m(v.omega_m) {}
 };
 template <> struct Par<float> {
-  float omega, rho0, qcut, F[3];
+  float omega, rho0, qcut, F[3], omega_m;
   __device__ __forceinline__ explicit Par(const View &v)
-      : omega(v.omega_f), rho0(v.rho0_f), qcut(v.qcut_f), F{v.F_f[0], v.F_f[1], v.F_f[2]} {}
+      : omega(v.omega_f), rho0(v.rho0_f), qcut(v.qcut_f), F{v.F_f[0], v.F_f[1], v.F_f[2]},
+        omega_m(v.omega_m_f) {}
 };
 
 // Relative element offsets of the 27 neighbours (dx, dy, dz in {-1,0,1}) of a node,

@@ -17,7 +17,8 @@ struct Launch {
 // Sets the shared-memory limit of the TMA-staged step kernel for this launch shape
 // and returns its persistent grid (SMs x resident blocks, at most ntiles) and its
 // dynamic shared memory. Call outside stream capture.
-cudaError_t prepare_step_tma(int lattice, int dtype, int has_force, int bx, int by, long long ntiles,
+// phys: PH_FORCE | PH_TRT bits of the view (see phys_of).
+cudaError_t prepare_step_tma(int lattice, int dtype, int phys, int bx, int by, long long ntiles,
                              int *blocks, int *smem);
 
 // lattice: 0 D2Q9, 1 D3Q19; dtype: 0 F64, 1 F32, 2 F16, 3 BF16

@@ -162,7 +162,7 @@ extern "C" int lbm_synchronize(lbm_handle h) {
 
 extern "C" int lbm_set_options(lbm_handle h, int bc, double rho0, const double force[3], int xshift) {
   if (!h) return lbm_fail(nullptr, LBM_ERR_ARG, "null handle");
-  if (bc < LBM_BC_ELIBB_F || bc > LBM_BC_HWBB) return lbm_fail(h, LBM_ERR_ARG, "unknown boundary rule");
+  if (bc < LBM_BC_ELIBB_F || bc > LBM_BC_ELIBB_UQ) return lbm_fail(h, LBM_ERR_ARG, "unknown boundary rule");
   if (bc == LBM_BC_BFL && h->mb.on)
     return lbm_fail(h, LBM_ERR_ARG, "BFL needs a second node along the link, which a moving body's records do not carry");
   if (!(rho0 > 0.0) || !std::isfinite(rho0)) return lbm_fail(h, LBM_ERR_ARG, "rho0 must be positive");
@@ -198,6 +198,19 @@ extern "C" int lbm_set_options(lbm_handle h, int bc, double rho0, const double f
   return LBM_OK;
 }
 
+extern "C" int lbm_set_collision(lbm_handle h, int model, double magic) {
+  if (!h) return lbm_fail(nullptr, LBM_ERR_ARG, "null handle");
+  if (model != LBM_COLL_BGK && model != LBM_COLL_TRT) return lbm_fail(h, LBM_ERR_ARG, "unknown collision model");
+  if (model == LBM_COLL_TRT && !(magic > 0.0 && std::isfinite(magic)))
+    return lbm_fail(h, LBM_ERR_ARG, "the TRT magic parameter must be positive");
+  h->collision = model;
+  if (model == LBM_COLL_TRT) h->magic = magic;
+  h->drop_graphs();
+  h->tiles_var = -1;  // the TMA-staged step is prepared per collision
+  ++h->version;
+  return LBM_OK;
+}
+
 // ---------------------------------------------------------------- kernel view, launch shapes
 View lbm_sim::view() const {
   View v;
@@ -206,7 +219,11 @@ View lbm_sim::view() const {
   v.omega = 1.0 / tau; v.rho0 = rho0; v.qcut = qcut;
   for (int a = 0; a < 3; ++a) v.F[a] = F[a];
   v.has_force = has_force; v.has_uw = has_uw;
+  v.trt = collision == LBM_COLL_TRT ? 1 : 0;
+  // Eq. magic-parameter with omega+ = 1/tau, solved for omega-
+  v.omega_m = v.trt ? 1.0 / (0.5 + magic / (tau - 0.5)) : v.omega;
   v.omega_f = (float)v.omega; v.rho0_f = (float)rho0; v.qcut_f = (float)qcut;
+  v.omega_m_f = (float)v.omega_m;
   for (int a = 0; a < 3; ++a) v.F_f[a] = (float)F[a];
   v.flags = flags; v.cbase = cbase; v.rec = rec; v.rnode = rnode; v.nb = nb;
   v.err = err_dev;
@@ -284,7 +301,8 @@ int lbm_sim::ensure_tiles() {
   tiles_by = step_by;
   tiles_var = variant;
   if (variant == 4) {
-    cudaError_t e = prepare_step_tma(lattice, dtype, has_force, step_bx, step_by, ntiles, &tma_blocks, &tma_smem);
+    const int phys = (has_force ? PH_FORCE : 0) | (collision == LBM_COLL_TRT ? PH_TRT : 0);
+    cudaError_t e = prepare_step_tma(lattice, dtype, phys, step_bx, step_by, ntiles, &tma_blocks, &tma_smem);
     if (e != cudaSuccess) {
       tiles_bx = 0;
       return lbm_fail(this, LBM_ERR_CUDA, std::string("TMA-staged step: ") + cudaGetErrorString(e));

@@ -44,6 +44,8 @@ struct lbm_sim {
   long long np = 0;  // padded nodes (population plane length)
   long long N = 0;   // nodes
   double tau = 1.0, rho0 = 1.0, qcut = 0.01;
+  int collision = LBM_COLL_BGK;     // lbm_collision
+  double magic = 3.0 / 16.0;        // TRT magic parameter Lambda
   double F[3] = {0.0, 0.0, 0.0};
   int has_force = 0, bc = 0, xshift = 0;
 

@@ -12,15 +12,22 @@
 
 namespace lbm {
 
+// Compile-time physics (PH_FORCE, PH_TRT) of a view.
+inline int phys_of(const View &v) { return (v.has_force ? PH_FORCE : 0) | (v.trt ? PH_TRT : 0); }
+
 // The step grid is 1-D, one block per entry of the tile table (l.grid.x entries).
 template <class L, typename S, typename M, int MINB, bool PAIR = false>
 cudaError_t step_variant(const View &v, const void *fin, void *fout, const Launch &l) {
-  if (v.has_force)
-    k_step<L, S, M, MINB, true, PAIR><<<l.grid, l.block, 0, l.stream>>>(v, static_cast<const S *>(fin),
-                                                                        static_cast<S *>(fout));
-  else
-    k_step<L, S, M, MINB, false, PAIR><<<l.grid, l.block, 0, l.stream>>>(v, static_cast<const S *>(fin),
-                                                                         static_cast<S *>(fout));
+  const S *a = static_cast<const S *>(fin);
+  S *b = static_cast<S *>(fout);
+  switch (phys_of(v)) {
+    case PH_FORCE: k_step<L, S, M, MINB, PH_FORCE, PAIR><<<l.grid, l.block, 0, l.stream>>>(v, a, b); break;
+    case PH_TRT: k_step<L, S, M, MINB, PH_TRT, PAIR><<<l.grid, l.block, 0, l.stream>>>(v, a, b); break;
+    case PH_FORCE | PH_TRT:
+      k_step<L, S, M, MINB, PH_FORCE | PH_TRT, PAIR><<<l.grid, l.block, 0, l.stream>>>(v, a, b);
+      break;
+    default: k_step<L, S, M, MINB, 0, PAIR><<<l.grid, l.block, 0, l.stream>>>(v, a, b); break;
+  }
   return cudaGetLastError();
 }
 
@@ -45,7 +52,7 @@ inline int tma_stages(int stage_bytes, int optin) {
   return k > 16 ? 16 : k;
 }
 
-template <class L, typename S, typename M, bool FORCE>
+template <class L, typename S, typename M, int PHYS>
 cudaError_t tma_prepare(int bx, int by, long long ntiles, int *blocks, int *smem) {
   const int sb = tma_stage_bytes<L, S, M>(bx, by);
   int dev0 = 0, optin = 0;
@@ -55,7 +62,7 @@ cudaError_t tma_prepare(int bx, int by, long long ntiles, int *blocks, int *smem
   const int stages = tma_stages(sb, optin);
   if (stages < 2) return cudaErrorInvalidConfiguration;
   *smem = 128 + stages * sb;
-  auto kern = k_step_tma<L, S, M, FORCE>;
+  auto kern = k_step_tma<L, S, M, PHYS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0, per = 0;
@@ -70,11 +77,11 @@ cudaError_t tma_prepare(int bx, int by, long long ntiles, int *blocks, int *smem
   return cudaSuccess;
 }
 
-template <class L, typename S, typename M, bool FORCE>
+template <class L, typename S, typename M, int PHYS>
 cudaError_t tma_launch(const View &v, const void *fin, void *fout, const Launch &l) {
   const int sb = tma_stage_bytes<L, S, M>(l.block.x, l.block.y);
   const int stages = (l.smem - 128) / sb;
-  k_step_tma<L, S, M, FORCE><<<l.grid, l.block, l.smem, l.stream>>>(
+  k_step_tma<L, S, M, PHYS><<<l.grid, l.block, l.smem, l.stream>>>(
       v, static_cast<const S *>(fin), static_cast<S *>(fout), stages, sb);
   return cudaGetLastError();
 }
@@ -89,8 +96,14 @@ cudaError_t launch_step_ls(int variant, const View &v, const void *fin, void *fo
   if constexpr (sizeof(M) == 8) {
     return step_variant<L, S, M, 1>(v, fin, fout, l);  // FP64: one register budget
   } else {
-    if (variant == 4)
-      return v.has_force ? tma_launch<L, S, M, true>(v, fin, fout, l) : tma_launch<L, S, M, false>(v, fin, fout, l);
+    if (variant == 4) {
+      switch (phys_of(v)) {
+        case PH_FORCE: return tma_launch<L, S, M, PH_FORCE>(v, fin, fout, l);
+        case PH_TRT: return tma_launch<L, S, M, PH_TRT>(v, fin, fout, l);
+        case PH_FORCE | PH_TRT: return tma_launch<L, S, M, PH_FORCE | PH_TRT>(v, fin, fout, l);
+        default: return tma_launch<L, S, M, 0>(v, fin, fout, l);
+      }
+    }
     switch (variant) {
       case 1: return step_variant<L, S, M, 2>(v, fin, fout, l);
       case 2: return step_variant<L, S, M, 3>(v, fin, fout, l);
@@ -104,13 +117,17 @@ cudaError_t launch_step_ls(int variant, const View &v, const void *fin, void *fo
 }
 
 template <class L, typename S>
-cudaError_t prepare_step_tma_ls(int has_force, int bx, int by, long long ntiles, int *blocks, int *smem) {
+cudaError_t prepare_step_tma_ls(int phys, int bx, int by, long long ntiles, int *blocks, int *smem) {
   using M = typename MathOf<S>::T;
   if constexpr (sizeof(M) == 8) {
     return cudaErrorInvalidValue;  // FP64 has no TMA-staged variant
   } else {
-    return has_force ? tma_prepare<L, S, M, true>(bx, by, ntiles, blocks, smem)
-                     : tma_prepare<L, S, M, false>(bx, by, ntiles, blocks, smem);
+    switch (phys) {
+      case PH_FORCE: return tma_prepare<L, S, M, PH_FORCE>(bx, by, ntiles, blocks, smem);
+      case PH_TRT: return tma_prepare<L, S, M, PH_TRT>(bx, by, ntiles, blocks, smem);
+      case PH_FORCE | PH_TRT: return tma_prepare<L, S, M, PH_FORCE | PH_TRT>(bx, by, ntiles, blocks, smem);
+      default: return tma_prepare<L, S, M, 0>(bx, by, ntiles, blocks, smem);
+    }
   }
 }
 

@@ -20,11 +20,14 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "lbm.h")
 
 D2Q9, D3Q19 = 0, 1
 F64, F32, F16, BF16 = 0, 1, 2, 3
-BC_ELIBB_F, BC_ELIBB_FQ, BC_BFL, BC_HWBB = 0, 1, 2, 3
+BC_ELIBB_F, BC_ELIBB_FQ, BC_BFL, BC_HWBB, BC_ELIBB_U, BC_ELIBB_UQ = 0, 1, 2, 3, 4, 5
+COLL_BGK, COLL_TRT = 0, 1
 FLUID, SOLID, OPEN = 0, 1, 2
 SHAPE_TYPES = {"sphere": 0, "sphere_out": 1, "ellipsoid": 2, "strip": 3}
 DTYPES = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
-BCS = {"elibb_f": BC_ELIBB_F, "elibb_fq": BC_ELIBB_FQ, "bfl": BC_BFL, "hwbb": BC_HWBB}
+BCS = {"elibb_f": BC_ELIBB_F, "elibb_fq": BC_ELIBB_FQ, "bfl": BC_BFL, "hwbb": BC_HWBB,
+       "elibb_u": BC_ELIBB_U, "elibb_uq": BC_ELIBB_UQ}
+COLLISIONS = {"bgk": COLL_BGK, "trt": COLL_TRT}
 STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_OOM",
           -4: "LBM_ERR_NONFINITE", -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_STATE"}
 
@@ -53,6 +56,7 @@ _SIGS = {
     "lbm_create": [ctypes.c_int, _int, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, P(ctypes.c_void_p)],
     "lbm_destroy": [ctypes.c_void_p],
     "lbm_set_options": [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, _d, ctypes.c_int],
+    "lbm_set_collision": [ctypes.c_void_p, ctypes.c_int, ctypes.c_double],
     "lbm_set_geometry": [ctypes.c_void_p, _u8, _d, _d, _d, _i32],
     "lbm_build_geometry": [ctypes.c_void_p, _u8, _d, P(Shape), ctypes.c_int],
     "lbm_init": [ctypes.c_void_p, ctypes.c_double, _d],
@@ -186,6 +190,11 @@ class Simulation:
         bc = BCS[bc] if isinstance(bc, str) else bc
         F = (ctypes.c_double * 3)(*[float(x) for x in force])
         self._ok(self.lib.lbm_set_options(self.h, bc, float(rho0), F, int(xshift)))
+
+    def set_collision(self, model=COLL_BGK, magic=3.0 / 16.0):
+        """BGK or TRT (magic parameter Lambda, Eq. magic-parameter)."""
+        model = COLLISIONS[model] if isinstance(model, str) else model
+        self._ok(self.lib.lbm_set_collision(self.h, int(model), float(magic)))
 
     def set_geometry(self, flags, q=None, uw=None, uw1=None, tag=None):
         """Host arrays in the library's direction order: flags[N], q[N,Q], uw[N,Q,3], tag[N,Q]."""

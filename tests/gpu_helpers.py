@@ -8,7 +8,9 @@ from paper_2009_04604_gb300 import lbm
 ORACLE_SHAPES = {"sphere": oracle.SHAPE_SPHERE, "sphere_out": oracle.SHAPE_SPHERE_OUT,
                  "ellipsoid": oracle.SHAPE_ELLIPSOID, "strip": oracle.SHAPE_STRIP}
 ORACLE_BC = {lbm.BC_ELIBB_F: oracle.BC_ELIBB_F, lbm.BC_ELIBB_FQ: oracle.BC_ELIBB_FQ,
-             lbm.BC_BFL: oracle.BC_BFL, lbm.BC_HWBB: oracle.BC_HWBB}
+             lbm.BC_BFL: oracle.BC_BFL, lbm.BC_HWBB: oracle.BC_HWBB,
+             lbm.BC_ELIBB_U: oracle.BC_ELIBB_U, lbm.BC_ELIBB_UQ: oracle.BC_ELIBB_UQ}
+ORACLE_COLL = {lbm.COLL_BGK: oracle.COLL_BGK, lbm.COLL_TRT: oracle.COLL_TRT}
 
 
 def perm(lat):
@@ -41,12 +43,16 @@ def oracle_shapes(shapes):
 def oracle_params(wl, bc=lbm.BC_ELIBB_F):
     return oracle.params(wl["lattice"], wl["dims"], wl["tau"], bc=ORACLE_BC[bc],
                          rho0=wl.get("rho0", 1.0), force=wl.get("force", (0, 0, 0)),
-                         xshift=wl.get("xshift", 0))
+                         xshift=wl.get("xshift", 0),
+                         collision=ORACLE_COLL[wl.get("collision", lbm.COLL_BGK)],
+                         magic=wl.get("magic", 3.0 / 16.0))
 
 
 def gpu_sim(wl, dtype, bc=lbm.BC_ELIBB_F):
     s = lbm.Simulation(wl["lattice"], wl["dims"], wl["tau"], dtype)
     s.set_options(bc, wl.get("rho0", 1.0), wl.get("force", (0, 0, 0)), wl.get("xshift", 0))
+    if wl.get("collision", lbm.COLL_BGK) != lbm.COLL_BGK:
+        s.set_collision(wl["collision"], wl.get("magic", 3.0 / 16.0))
     return s
 
 
