@@ -29,6 +29,7 @@ FLUID, SOLID, OPEN = 0, 1, 2
 BC_ELIBB_F, BC_ELIBB_FQ, BC_BFL, BC_HWBB, BC_ELIBB_U, BC_ELIBB_UQ = 0, 1, 2, 3, 4, 5
 SHAPE_SPHERE, SHAPE_SPHERE_OUT, SHAPE_ELLIPSOID, SHAPE_STRIP = 0, 1, 2, 3
 COLL_BGK, COLL_TRT = 0, 1
+NEQ_BOUNCE_BACK, NEQ_REGULARIZED = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -53,7 +54,8 @@ class Params(ctypes.Structure):
                 ("tau", ctypes.c_double), ("rho0", ctypes.c_double),
                 ("force", ctypes.c_double * 3), ("qcut", ctypes.c_double),
                 ("wall_neq_same", ctypes.c_int), ("me_rho0", ctypes.c_int),
-                ("s1_exact", ctypes.c_int), ("collision", ctypes.c_int), ("magic", ctypes.c_double)]
+                ("s1_exact", ctypes.c_int), ("collision", ctypes.c_int), ("wall_neq", ctypes.c_int),
+                ("magic", ctypes.c_double)]
 
 
 class Shape(ctypes.Structure):
@@ -107,7 +109,8 @@ def lattice(lat: int):
 
 
 def params(lattice_id, dims, tau, bc=BC_ELIBB_F, rho0=1.0, force=(0.0, 0.0, 0.0), xshift=0,
-           qcut=0.01, wall_neq_same=0, me_rho0=0, s1_exact=0, collision=0, magic=0.1875) -> Params:
+           qcut=0.01, wall_neq_same=0, me_rho0=0, s1_exact=0, collision=0, magic=0.1875,
+           wall_neq=0) -> Params:
     nx, ny, nz = (list(dims) + [1, 1])[:3]
     p = Params()
     p.lattice, p.nx, p.ny, p.nz, p.xshift, p.bc = lattice_id, nx, ny, nz, xshift, bc
@@ -115,7 +118,7 @@ def params(lattice_id, dims, tau, bc=BC_ELIBB_F, rho0=1.0, force=(0.0, 0.0, 0.0)
     for a in range(3):
         p.force[a] = float(force[a])
     p.wall_neq_same, p.me_rho0, p.s1_exact = wall_neq_same, me_rho0, s1_exact
-    p.collision, p.magic = collision, magic
+    p.collision, p.magic, p.wall_neq = collision, magic, wall_neq
     return p
 
 

@@ -10,6 +10,7 @@
  *   Lattice Boltzmann equation ............ Sec. II.A, Eq. LBE
  *   BGK collision, Omega = 1/tau .......... Sec. II.A, Eq. LB-BGK
  *   TRT collision (even/odd rates) ........ Sec. II.A, TRT paragraph, Eq. magic-parameter
+ *   regularized wall non-equilibrium ...... appendix, Eqs. fi_neq, malaspinas, a12Eqlambda
  *   second-order equilibrium .............. Sec. II.A, Eq. Eq2ndOrder (c_s^2 = 1/3)
  *   generic interpolated bounce-back ...... Sec. II.B, Eq. general-ibb-linear
  *   BFL (linear Bouzidi) .................. Sec. II.B, Eq. bfl
@@ -31,6 +32,10 @@
  *     at first order);
  *   - TRT with Guo forcing: the even and odd parts of the forcing term take the
  *     factors (1 - omega+/2) and (1 - omega-/2);
+ *   - regularized wall non-equilibrium (Eq. fi_neq, third-order truncation): the
+ *     second Hermite coefficient is the node's non-equilibrium stress (Lambda at
+ *     the wall taken as at x_F), the third follows from Eq. malaspinas with the
+ *     wall's velocity at each wall point's time; open links keep Eq. neqbb-s;
  *   - the wall population index is i (incoming), as the paper's macros write it;
  *   - rho in the wall equilibria and the moving-wall term is rho_F(t);
  *   - the force uses the outgoing post-collision population f*_ibar (Wen et al.);
@@ -148,6 +153,30 @@ static double trt_post(const lat_t *L, int i, const double *fn, double rho, cons
   const double si = guo_term(L, i, u, F), sb = guo_term(L, ib, u, F);
   const double sp = 0.5 * (si + sb), sm = 0.5 * (si - sb);
   return fn[i] - omp * (fp - ep) - omm * (fm - em) + (1.0 - 0.5 * omp) * sp + (1.0 - 0.5 * omm) * sm;
+}
+
+/* ---- regularized non-equilibrium (appendix, Eq. fi_neq) ----
+ * Hermite tensors H2_ab = c_a c_b - cs2 d_ab and
+ * H3_abc = c_a c_b c_c - cs2 (c_a d_bc + c_b d_ac + c_c d_ab). The first-order
+ * population is rebuilt from its second Hermite coefficient a2 (the
+ * non-equilibrium stress) and the third, a3_abc = u_c a2_ab + u_b a2_ac + u_a a2_bc
+ * (Eq. malaspinas, isothermal):
+ *   f1_i = w_i [ H2_i : a2 / (2 cs2^2) + H3_i : a3 / (6 cs2^3) ]                 */
+static double kd(int a, int b) { return a == b ? 1.0 : 0.0; }
+
+static double reg_neq(const lat_t *L, int i, const double a2[3][3], const double u[3]) {
+  const int *c = L->c[i];
+  double s2 = 0.0, s3 = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      s2 += (c[a] * c[b] - CS2 * kd(a, b)) * a2[a][b];
+      for (int g = 0; g < 3; ++g) {
+        const double h3 = c[a] * c[b] * c[g] - CS2 * (c[a] * kd(b, g) + c[b] * kd(a, g) + c[g] * kd(a, b));
+        const double a3 = u[g] * a2[a][b] + u[b] * a2[a][g] + u[a] * a2[b][g];
+        s3 += h3 * a3;
+      }
+    }
+  return L->w[i] * (s2 / (2.0 * CS2 * CS2) + s3 / (6.0 * CS2 * CS2 * CS2));
 }
 
 /* density and Guo-corrected velocity u = (sum c f + F/2) / rho */
@@ -302,6 +331,15 @@ int or_step(const or_params *p, const uint8_t *flags, const double *q, const dou
     int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long)nx * ny));
     const double rF = rho[n];
     const double *uF = vel + n * 3;
+    /* non-equilibrium stress of the node, sum_j c_j c_j (f_j - f^eq_j), for the
+     * regularized wall estimate (the stress at the wall is taken as the node's) */
+    double a2[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+    if (p->wall_neq == OR_NEQ_REGULARIZED)
+      for (int j = 0; j < Q; ++j) {
+        const double fn = f[n * Q + j] - feq(&L, j, rF, uF);
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) a2[a][b] += L.c[j][a] * L.c[j][b] * fn;
+      }
     for (int i = 1; i < Q; ++i) {
       long m = nbr(p, x, y, z, -L.c[i][0], -L.c[i][1], -L.c[i][2]);
       if (flags[m] == OR_FLUID) continue;
@@ -328,8 +366,13 @@ int or_step(const or_params *p, const uint8_t *flags, const double *q, const dou
       /* reading: under TRT the wall non-equilibrium, even in c at first order, decays
        * with omega+ = 1/tau as under BGK */
       const double post = p->wall_neq_same ? 1.0 : (1.0 - omega);
-      const double f0 = feq(&L, i, rF, u1) + fneq_ib;
-      const double f1 = feq(&L, i, rF, u0) + post * fneq_ib;
+      /* wall non-equilibrium: f^neq_ibar(x_F) (Eq. neqbb-s), or the regularized
+       * estimate with the wall's velocity at each time (Eq. fi_neq) */
+      const int reg = p->wall_neq == OR_NEQ_REGULARIZED;
+      const double fn0 = reg ? reg_neq(&L, i, (const double(*)[3])a2, u1) : fneq_ib;
+      const double fn1 = reg ? reg_neq(&L, i, (const double(*)[3])a2, u0) : fneq_ib;
+      const double f0 = feq(&L, i, rF, u1) + fn0;
+      const double f1 = feq(&L, i, rF, u0) + post * fn1;
       const double s1 = p->s1_exact ? 1.0 + cu / c2 : 1.0;
       /* second fluid node along the link (BFL only) */
       long ff = nbr(p, x, y, z, L.c[i][0], L.c[i][1], L.c[i][2]);

@@ -33,6 +33,9 @@ enum { OR_BC_ELIBB_F = 0, OR_BC_ELIBB_FQ = 1, OR_BC_BFL = 2, OR_BC_HWBB = 3,
 /* Collision operators: single relaxation time (Eq. LB-BGK) and two relaxation
  * times (Sec. II.A, TRT paragraph). */
 enum { OR_COLL_BGK = 0, OR_COLL_TRT = 1 };
+/* Estimates of the non-equilibrium part of a wall population (Sec. II.C.1 and
+ * the appendix on the regularized reconstruction). */
+enum { OR_NEQ_BOUNCE_BACK = 0, OR_NEQ_REGULARIZED = 1 };
 /* Analytic shapes for the link geometry. */
 enum { OR_SHAPE_SPHERE = 0,      /* solid inside |x-c| <= r0 (circle in 2D)        */
        OR_SHAPE_SPHERE_OUT = 1,  /* solid outside |x-c| >= r0                      */
@@ -55,6 +58,8 @@ typedef struct {
   int s1_exact;       /* 0: s of the post-collision wall population is 1 (default);
                          1: s = 1 + u_w.c_i/|c_i|^2 (Eq. x_to_s_helper as printed) */
   int collision;      /* OR_COLL_BGK, or OR_COLL_TRT (two relaxation times, Sec. II.A) */
+  int wall_neq;       /* OR_NEQ_BOUNCE_BACK (Eq. neqbb-s) or OR_NEQ_REGULARIZED (Eq. fi_neq):
+                         the estimate of the wall non-equilibrium in the ELIBB wall populations */
   double magic;       /* TRT: Lambda = (1/omega+ - 1/2)(1/omega- - 1/2) (Eq. magic-parameter),
                          omega+ = 1/tau */
 } or_params;
