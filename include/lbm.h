@@ -63,6 +63,8 @@ enum lbm_bc { LBM_BC_ELIBB_F = 0, LBM_BC_ELIBB_FQ = 1, LBM_BC_BFL = 2, LBM_BC_HW
 /* Collision operators: BGK (Sec. II.A, Eq. LB-BGK) and two relaxation times
  * (Sec. II.A, TRT paragraph, Eq. magic-parameter). */
 enum lbm_collision { LBM_COLL_BGK = 0, LBM_COLL_TRT = 1 };
+/* Estimates of the non-equilibrium part of the ELIBB wall populations (Sec. II.D). */
+enum lbm_wall_neq { LBM_NEQ_BOUNCE_BACK = 0, LBM_NEQ_REGULARIZED = 1 };
 
 /* Node kinds. A link into an OPEN node gets the single-node pressure rule
  * f_i = f_i^eq(rho0, u_F) + f^neq_ibar(x_F), the non-equilibrium bounce-back of
@@ -126,6 +128,19 @@ int lbm_set_options(lbm_handle h, int bc, double rho0, const double force[3], in
  * wall estimate keeps the factor (1 - omega+). magic is ignored for BGK and must
  * be positive for TRT; otherwise LBM_ERR_ARG. Takes effect at the next step. */
 int lbm_set_collision(lbm_handle h, int model, double magic);
+
+/* Non-equilibrium part of the ELIBB wall populations (lbm_wall_neq):
+ *   NEQ_BOUNCE_BACK (default): f^neq_ibar(x_F), the node's own opposite
+ *     population (Eq. neqbb-s);
+ *   NEQ_REGULARIZED: the Hermite reconstruction of the appendix's Eq. fi_neq,
+ *     truncated at third order. The second-order coefficient is the node's
+ *     non-equilibrium stress (the wall's stress taken as the node's); the third
+ *     follows from the isothermal recursion (Eq. malaspinas) with the wall
+ *     velocity at each wall population's time. On D3Q19, which lacks part of the
+ *     third-order Hermite set, the reconstruction is exact up to O(Ma^2).
+ * Open (outlet) links keep the bounce-back estimate. Takes effect at the next
+ * step; LBM_ERR_ARG for an unknown mode. */
+int lbm_set_wall_neq(lbm_handle h, int mode);
 
 /* Explicit geometry from host arrays.
  *   flags[N]: lbm_node per node.

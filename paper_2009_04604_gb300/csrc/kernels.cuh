@@ -313,9 +313,60 @@ __device__ __forceinline__ int upstream_offset(const View &v, int x, int y, int 
   return ((Z - z) * v.ny + (Y - y)) * v.nxp + (X - x);
 }
 
+// Non-equilibrium stress of a node, Pi_ab = sum_j c_ja c_jb (f_j - f^eq_j), from
+// its shifted populations: Pi = sum_j c_j c_j f~_j - drho c_s^2 I - rho u u (in
+// the lattice's own dimensions).
+// Components xx, yy, zz, xy, xz, yz.
+template <class L, typename M>
+__device__ __forceinline__ void neq_stress(const M (&f)[L::Q], const Macro<L, M> &m, M (&pi)[6]) {
+  using X = Ex<M>;
+  M s[6] = {M(0), M(0), M(0), M(0), M(0), M(0)};
+#pragma unroll
+  for (int j = 0; j < L::Q; ++j) {
+    const int cx = L::cx(j), cy = L::cy(j), cz = L::cz(j);
+    if (cx) s[0] = X::add(s[0], f[j]);
+    if (cy) s[1] = X::add(s[1], f[j]);
+    if (cz) s[2] = X::add(s[2], f[j]);
+    if (cx * cy) s[3] = cx * cy > 0 ? X::add(s[3], f[j]) : X::sub(s[3], f[j]);
+    if (cx * cz) s[4] = cx * cz > 0 ? X::add(s[4], f[j]) : X::sub(s[4], f[j]);
+    if (cy * cz) s[5] = cy * cz > 0 ? X::add(s[5], f[j]) : X::sub(s[5], f[j]);
+  }
+  const M d = X::mul(m.drho, M(1.0 / 3.0));
+  const M ru[3] = {X::mul(m.rho, m.ux), X::mul(m.rho, m.uy), X::mul(m.rho, m.uz)};
+  pi[0] = X::sub(X::sub(s[0], d), X::mul(ru[0], m.ux));
+  pi[1] = X::sub(X::sub(s[1], d), X::mul(ru[1], m.uy));
+  // a 2-D lattice has no z velocities: its equilibrium has no zz moment either
+  pi[2] = L::D == 2 ? M(0) : X::sub(X::sub(s[2], d), X::mul(ru[2], m.uz));
+  pi[3] = X::sub(s[3], X::mul(ru[0], m.uy));
+  pi[4] = X::sub(s[4], X::mul(ru[0], m.uz));
+  pi[5] = X::sub(s[5], X::mul(ru[1], m.uz));
+}
+
+// Regularized estimate of the non-equilibrium part of wall population i (the
+// appendix's Eq. fi_neq, third-order truncation): with a2 = Pi and, by Eq.
+// malaspinas, a3_abc = u_c Pi_ab + u_b Pi_ac + u_a Pi_bc (u the wall velocity),
+//   f1_i = w_i [H2_i : a2 / (2 c_s^4) + H3_i : a3 / (6 c_s^6)]
+//        = w_i [9/2 (c.Pi.c) - 3/2 tr Pi + 27/2 (c.u)(c.Pi.c) - 9/2 (2 c.Pi.u + (c.u) tr Pi)].
+template <class L, typename M>
+__device__ __forceinline__ M neq_regularized(int i, const M (&pi)[6], M ux, M uy, M uz) {
+  using X = Ex<M>;
+  const M cx = M(dcx<L>(i)), cy = M(dcy<L>(i)), cz = M(dcz<L>(i));
+  const M pcx = X::fma(cz, pi[4], X::fma(cy, pi[3], X::mul(cx, pi[0])));  // (Pi c)_x
+  const M pcy = X::fma(cz, pi[5], X::fma(cy, pi[1], X::mul(cx, pi[3])));  // (Pi c)_y
+  const M pcz = X::fma(cz, pi[2], X::fma(cy, pi[5], X::mul(cx, pi[4])));  // (Pi c)_z
+  const M cpc = X::fma(cz, pcz, X::fma(cy, pcy, X::mul(cx, pcx)));
+  const M cpu = X::fma(uz, pcz, X::fma(uy, pcy, X::mul(ux, pcx)));
+  const M tr = X::add(X::add(pi[0], pi[1]), pi[2]);
+  const M cu = cdot_r<L, M>(i, ux, uy, uz);
+  const M t2 = X::fma(M(4.5), cpc, X::mul(M(-1.5), tr));
+  const M t3 = X::fma(X::mul(M(13.5), cu), cpc, X::mul(M(-4.5), X::fma(M(2), cpu, X::mul(cu, tr))));
+  return X::mul(dweight<L, M>(i), X::add(t2, t3));
+}
+
 template <class L, typename S, typename M>
 __device__ void boundary(const View &v, const RecSet &rs, const Rec &r, const M *fs, int stride,
-                         const Macro<L, M> &m, long long n, int x, int y, int z, S *__restrict__ fout) {
+                         const Macro<L, M> &m, const M (&pi)[6], long long n, int x, int y, int z,
+                         S *__restrict__ fout) {
   using X = Ex<M>;
   const M *lq = static_cast<const M *>(rs.lq);
   const M *luw = static_cast<const M *>(rs.luw);
@@ -361,13 +412,18 @@ __device__ void boundary(const View &v, const RecSet &rs, const Rec &r, const M 
           val = X::div(X::fma(a, h, g), q2);
         }
       } else {
+        // wall non-equilibrium: f^neq_ibar(x_F) (Eq. neqbb-s), or the regularized
+        // estimate with the wall velocity of each wall point's time (Eq. fi_neq)
         const M fneq_ib = X::sub(fib, feq_r<L, M>(ib, m.drho, m.rho, m.ux, m.uy, m.uz, m.usq));
+        const bool reg = v.wall_neq != 0;
+        const M fn1 = reg ? neq_regularized<L, M>(i, pi, wx, wy, wz) : fneq_ib;
+        const M fn0 = reg ? neq_regularized<L, M>(i, pi, vx, vy, vz) : fneq_ib;
         const M u0sq = X::fma(wz, wz, X::fma(wy, wy, X::mul(wx, wx)));
-        const M f1 = X::fma(X::sub(M(1), P.omega), fneq_ib, feq_r<L, M>(i, m.drho, m.rho, wx, wy, wz, u0sq));
+        const M f1 = X::fma(X::sub(M(1), P.omega), fn1, feq_r<L, M>(i, m.drho, m.rho, wx, wy, wz, u0sq));
         const bool unified_lin = v.bc == BC_ELIBB_U || (v.bc == BC_ELIBB_UQ && omq < P.qcut);
         if (unified_lin || q < M(0.5) || v.bc == BC_ELIBB_UQ) {
           const M u1sq = X::fma(vz, vz, X::fma(vy, vy, X::mul(vx, vx)));
-          const M f0 = X::add(feq_r<L, M>(i, m.drho, m.rho, vx, vy, vz, u1sq), fneq_ib);
+          const M f0 = X::add(feq_r<L, M>(i, m.drho, m.rho, vx, vy, vz, u1sq), fn0);
           if (unified_lin)  // ELIBB-U: the wall points s = 0 and s = 1 only
             val = X::fma(q, f1, X::mul(omq, f0));
           else if ((v.bc == BC_ELIBB_FQ && q >= P.qcut) || v.bc == BC_ELIBB_UQ)
@@ -422,9 +478,11 @@ __device__ __forceinline__ void boundary_node(const View &v, const RecSet &rs, c
   gather<L, S, M>(v, fin, n, nb, f);
   if (v.bc == BC_BFL) bfl_complete<L, M>(v, r, f);
   const Macro<L, M> m = moments<L, M>(v, f);
+  M pi[6] = {M(0), M(0), M(0), M(0), M(0), M(0)};
+  if (v.wall_neq) neq_stress<L, M>(f, m, pi);
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) fs[i * stride] = f[i];
-  boundary<L, S, M>(v, rs, r, fs, stride, m, n, x, y, z, fout);
+  boundary<L, S, M>(v, rs, r, fs, stride, m, pi, n, x, y, z, fout);
 }
 
 // ---------------------------------------------------------------- the fused step

@@ -131,6 +131,7 @@ struct View {
   double F[3];               // body-force density
   int has_force, has_uw;
   int trt;                   // 1: TRT collision, odd parts relax with omega_m
+  int wall_neq;              // 0: non-equilibrium bounce-back, 1: regularized wall estimate
   double omega_m;            // TRT omega- (Eq. magic-parameter); equals omega under BGK
   // the same scalars in FP32, so that FP32 kernels convert nothing on the
   // (slow) FP64 pipe: omega, rho0, qcut, F, omega_m

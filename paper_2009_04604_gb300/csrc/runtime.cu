@@ -198,6 +198,16 @@ extern "C" int lbm_set_options(lbm_handle h, int bc, double rho0, const double f
   return LBM_OK;
 }
 
+extern "C" int lbm_set_wall_neq(lbm_handle h, int mode) {
+  if (!h) return lbm_fail(nullptr, LBM_ERR_ARG, "null handle");
+  if (mode != LBM_NEQ_BOUNCE_BACK && mode != LBM_NEQ_REGULARIZED)
+    return lbm_fail(h, LBM_ERR_ARG, "unknown wall non-equilibrium estimate");
+  h->wall_neq = mode;
+  h->drop_graphs();
+  ++h->version;
+  return LBM_OK;
+}
+
 extern "C" int lbm_set_collision(lbm_handle h, int model, double magic) {
   if (!h) return lbm_fail(nullptr, LBM_ERR_ARG, "null handle");
   if (model != LBM_COLL_BGK && model != LBM_COLL_TRT) return lbm_fail(h, LBM_ERR_ARG, "unknown collision model");
@@ -220,6 +230,7 @@ View lbm_sim::view() const {
   for (int a = 0; a < 3; ++a) v.F[a] = F[a];
   v.has_force = has_force; v.has_uw = has_uw;
   v.trt = collision == LBM_COLL_TRT ? 1 : 0;
+  v.wall_neq = wall_neq == LBM_NEQ_REGULARIZED ? 1 : 0;
   // Eq. magic-parameter with omega+ = 1/tau, solved for omega-
   v.omega_m = v.trt ? 1.0 / (0.5 + magic / (tau - 0.5)) : v.omega;
   v.omega_f = (float)v.omega; v.rho0_f = (float)rho0; v.qcut_f = (float)qcut;

@@ -46,6 +46,7 @@ struct lbm_sim {
   double tau = 1.0, rho0 = 1.0, qcut = 0.01;
   int collision = LBM_COLL_BGK;     // lbm_collision
   double magic = 3.0 / 16.0;        // TRT magic parameter Lambda
+  int wall_neq = LBM_NEQ_BOUNCE_BACK;  // lbm_wall_neq
   double F[3] = {0.0, 0.0, 0.0};
   int has_force = 0, bc = 0, xshift = 0;
 

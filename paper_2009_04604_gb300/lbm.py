@@ -22,6 +22,7 @@ D2Q9, D3Q19 = 0, 1
 F64, F32, F16, BF16 = 0, 1, 2, 3
 BC_ELIBB_F, BC_ELIBB_FQ, BC_BFL, BC_HWBB, BC_ELIBB_U, BC_ELIBB_UQ = 0, 1, 2, 3, 4, 5
 COLL_BGK, COLL_TRT = 0, 1
+NEQ_BOUNCE_BACK, NEQ_REGULARIZED = 0, 1
 FLUID, SOLID, OPEN = 0, 1, 2
 SHAPE_TYPES = {"sphere": 0, "sphere_out": 1, "ellipsoid": 2, "strip": 3}
 DTYPES = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
@@ -57,6 +58,7 @@ _SIGS = {
     "lbm_destroy": [ctypes.c_void_p],
     "lbm_set_options": [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, _d, ctypes.c_int],
     "lbm_set_collision": [ctypes.c_void_p, ctypes.c_int, ctypes.c_double],
+    "lbm_set_wall_neq": [ctypes.c_void_p, ctypes.c_int],
     "lbm_set_geometry": [ctypes.c_void_p, _u8, _d, _d, _d, _i32],
     "lbm_build_geometry": [ctypes.c_void_p, _u8, _d, P(Shape), ctypes.c_int],
     "lbm_init": [ctypes.c_void_p, ctypes.c_double, _d],
@@ -190,6 +192,10 @@ class Simulation:
         bc = BCS[bc] if isinstance(bc, str) else bc
         F = (ctypes.c_double * 3)(*[float(x) for x in force])
         self._ok(self.lib.lbm_set_options(self.h, bc, float(rho0), F, int(xshift)))
+
+    def set_wall_neq(self, mode=NEQ_BOUNCE_BACK):
+        """Wall non-equilibrium estimate: bounce-back (Eq. neqbb-s) or regularized (Eq. fi_neq)."""
+        self._ok(self.lib.lbm_set_wall_neq(self.h, int(mode)))
 
     def set_collision(self, model=COLL_BGK, magic=3.0 / 16.0):
         """BGK or TRT (magic parameter Lambda, Eq. magic-parameter)."""

@@ -45,7 +45,7 @@ def oracle_params(wl, bc=lbm.BC_ELIBB_F):
                          rho0=wl.get("rho0", 1.0), force=wl.get("force", (0, 0, 0)),
                          xshift=wl.get("xshift", 0),
                          collision=ORACLE_COLL[wl.get("collision", lbm.COLL_BGK)],
-                         magic=wl.get("magic", 3.0 / 16.0))
+                         magic=wl.get("magic", 3.0 / 16.0), wall_neq=wl.get("wall_neq", 0))
 
 
 def gpu_sim(wl, dtype, bc=lbm.BC_ELIBB_F):
@@ -53,6 +53,8 @@ def gpu_sim(wl, dtype, bc=lbm.BC_ELIBB_F):
     s.set_options(bc, wl.get("rho0", 1.0), wl.get("force", (0, 0, 0)), wl.get("xshift", 0))
     if wl.get("collision", lbm.COLL_BGK) != lbm.COLL_BGK:
         s.set_collision(wl["collision"], wl.get("magic", 3.0 / 16.0))
+    if wl.get("wall_neq", 0):
+        s.set_wall_neq(wl["wall_neq"])
     return s
 
 
