@@ -210,6 +210,13 @@ __device__ __forceinline__ void collide_store(const View &v, const M (&f)[L::Q],
   relax<L, M, PHYS>(v, f, m, [&](int i, M val) { dst[i * np] = to_store<S, M>(val); });
 }
 
+// The same, storing node n's planes at the view's precomputed plane offsets.
+template <class L, typename S, typename M, int PHYS>
+__device__ __forceinline__ void collide_store_at(const View &v, const M (&f)[L::Q], const Macro<L, M> &m,
+                                                 S *__restrict__ fout, int n) {
+  relax<L, M, PHYS>(v, f, m, [&](int i, M val) { fout[v.soff[i] + n] = to_store<S, M>(val); });
+}
+
 template <class L, typename M, int PHYS>
 __device__ __forceinline__ void post_all(const View &v, const M (&f)[L::Q], const Macro<L, M> &m,
                                          M (&out)[L::Q]) {
@@ -525,13 +532,9 @@ __device__ __forceinline__ void lattice_tile(const View &v, const S *__restrict_
                         (L::D == 2 || (z > 0 && z < v.nz - 1));
   if (interior) {
     // no wrap: the source of population i is n - c_i, at an offset that is the same
-    // for every thread, so each load is a per-thread base plus a uniform offset
-    const int plane = v.nxp * v.ny;
+    // for every thread and precomputed on the host (loff)
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-      const S *__restrict__ p = fin + (i * np - (L::cx(i) + L::cy(i) * v.nxp + L::cz(i) * plane));
-      f[i] = to_math<S, M>(__ldg(p + n));
-    }
+    for (int i = 0; i < L::Q; ++i) f[i] = to_math<S, M>(__ldg(fin + (v.loff[i] + n)));
   } else {
     Nbr nb;
     nb.init(v, x, y, z);
@@ -542,7 +545,7 @@ __device__ __forceinline__ void lattice_tile(const View &v, const S *__restrict_
   }
   if (v.bc == BC_BFL && (fl & F_BOUNDARY)) bfl_complete<L, M>(v, *record_of(v, n, bal), f);
   const Macro<L, M> m = moments<L, M>(v, f);
-  collide_store<L, S, M, PHYS>(v, f, m, fout + n, np);
+  collide_store_at<L, S, M, PHYS>(v, f, m, fout, n);
 }
 
 // ---------------------------------------------------------------- two nodes per thread
@@ -608,7 +611,7 @@ __device__ __forceinline__ void lattice_tile_pair(const View &v, const S *__rest
   T p[L::Q];
 #pragma unroll
   for (int i = 0; i < L::Q; ++i)
-    p[i] = __ldg(reinterpret_cast<const T *>(fin + (long long)i * np + n + ro[1 - L::cy(i)][1 - L::cz(i)]));
+    p[i] = __ldg(reinterpret_cast<const T *>(fin + (v.soff[i] + n + ro[1 - L::cy(i)][1 - L::cz(i)])));
   // the element per x-shifted plane that the neighbouring lanes cannot supply:
   // c_ix = +1: x-1 at lane 0 (wrapping when x = 0); c_ix = -1: x+1 when it leaves
   // the row (node x+1 is then padding), else x+2 at lane 31 or when it wraps
@@ -653,7 +656,7 @@ __device__ __forceinline__ void lattice_tile_pair(const View &v, const S *__rest
   if (fa && fb) {
 #pragma unroll
     for (int i = 0; i < L::Q; ++i)
-      *reinterpret_cast<T *>(fout + (long long)i * np + n) = V::make(pa[i], pb[i]);
+      *reinterpret_cast<T *>(fout + (v.soff[i] + n)) = V::make(pa[i], pb[i]);
   } else {
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {

@@ -143,6 +143,10 @@ struct View {
   long long nb;              // number of boundary records
   const int2 *tiles;         // step-kernel block table (see k_step)
   int gx;                    // lattice tiles per row of tiles (nxp / block x)
+  // per-direction element offsets, computed on the host so that the kernels use
+  // them as constant operands: soff[i] = i np (plane i), loff[i] = i np - (c_ix +
+  // c_iy nxp + c_iz nxp ny) (the source of population i at an interior node)
+  int soff[19], loff[19];
   int ntiles, tpb_tiles;     // table length; consecutive table entries per block
   // moving body: records of the nodes of its region, rebuilt every step
   RecSet dyn;

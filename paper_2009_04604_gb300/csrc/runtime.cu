@@ -239,6 +239,12 @@ View lbm_sim::view() const {
   v.flags = flags; v.cbase = cbase; v.rec = rec; v.rnode = rnode; v.nb = nb;
   v.err = err_dev;
   v.tiles = tiles; v.gx = nxp / (step_bx * npt());
+  for (int i = 0; i < Q; ++i) {
+    int c[3];
+    lattice_c(i, c[0], c[1], c[2]);
+    v.soff[i] = (int)((long long)i * np);
+    v.loff[i] = (int)((long long)i * np - (c[0] + (long long)c[1] * nxp + (long long)c[2] * nxp * ny));
+  }
   v.ntiles = (int)ntiles; v.tpb_tiles = tiles_per_block;
   if (mb.on) {
     v.dyn = RecSet{mb.rec[cur], mb.rnode[cur], mb.lq[cur], mb.luw[cur], mb.luw1[cur], mb.ltag[cur]};
