@@ -913,7 +913,7 @@ __global__ void __launch_bounds__(256, 2) k_step_tma(const View v, const S *__re
 // force, collision operator), and one launch covers one class, compiled for it
 // (PHYS) as k_step is. The per-node code is the same as k_step's, so a batched
 // simulation gives exactly the results it gives when stepped alone.
-struct BatchEntry {
+struct alignas(16) BatchEntry {
   View v;
   const void *f0;  // read on even batch steps
   void *f1;        // read on odd batch steps
@@ -931,7 +931,13 @@ __global__ void __launch_bounds__(256, MINB) k_step_batch(const BatchEntry *__re
     if (idx >= ntiles) break;  // uniform across the block
     const int4 tile = tiles[idx];
     __syncthreads();  // the previous tile is done with se
-    if (t == 0) se = entries[tile.x];
+    {  // the first warp copies the entry in 16-byte pieces
+      constexpr int kPieces = (int)(sizeof(BatchEntry) / 16);
+      const int4 *src = reinterpret_cast<const int4 *>(entries + tile.x);
+      int4 *dst = reinterpret_cast<int4 *>(&se);
+      if (t < 32)
+        for (int k = t; k < kPieces; k += 32) dst[k] = __ldg(src + k);
+    }
     __syncthreads();
     const S *fin = static_cast<const S *>(parity ? se.f1 : se.f0);
     S *fout = static_cast<S *>(parity ? const_cast<void *>(se.f0) : se.f1);
