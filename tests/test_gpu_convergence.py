@@ -89,3 +89,13 @@ def test_circular_couette_second_order(bc, dtype, sizes, rtol, scaled):
           f"orders={['%.2f' % o for o in order]} fitted={slope:.2f}")
     assert slope > 1.8, (err, order)
     assert min(order) > 1.5, (err, order)
+
+
+@pytest.mark.parametrize("tau", [0.6, 1.0])
+def test_circular_couette_second_order_other_tau(tau):
+    """The configuration's other relaxation times, ELIBB-F in FP64 (tau = 0.8 above)."""
+    sizes = (64, 128, 256)
+    err = [_steady_error(lbm.BC_ELIBB_F, L, lbm.F64, 1e-9, True, tau=tau)[0] for L in sizes]
+    slope = -np.polyfit(np.log(sizes), np.log(err), 1)[0]
+    print(f"tau={tau} L={sizes} rRSE={['%.3e' % e for e in err]} fitted={slope:.2f}")
+    assert slope > 1.8, err
