@@ -24,7 +24,7 @@ _LIB_PATH = os.path.join(_BUILD, "liblbm_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-D2Q9, D3Q19 = 0, 1
+D2Q9, D3Q19, D3Q27 = 0, 1, 2
 FLUID, SOLID, OPEN = 0, 1, 2
 BC_ELIBB_F, BC_ELIBB_FQ, BC_BFL, BC_HWBB, BC_ELIBB_U, BC_ELIBB_UQ = 0, 1, 2, 3, 4, 5
 SHAPE_SPHERE, SHAPE_SPHERE_OUT, SHAPE_ELLIPSOID, SHAPE_STRIP = 0, 1, 2, 3
@@ -101,9 +101,9 @@ def _dp(a):
 def lattice(lat: int):
     """Oracle lattice tables ``(c[Q,3] int, w[Q], opp[Q])``."""
     lib = _load()
-    c = np.zeros((19, 3), np.int32)
-    w = np.zeros(19)
-    opp = np.zeros(19, np.int32)
+    c = np.zeros((27, 3), np.int32)
+    w = np.zeros(27)
+    opp = np.zeros(27, np.int32)
     Qn = lib.or_lattice(lat, _ptr(c, ctypes.c_int), _dp(w), _ptr(opp, ctypes.c_int))
     return c[:Qn].copy(), w[:Qn].copy(), opp[:Qn].copy()
 
@@ -123,7 +123,7 @@ def params(lattice_id, dims, tau, bc=BC_ELIBB_F, rho0=1.0, force=(0.0, 0.0, 0.0)
 
 
 def _Q(p):
-    return 9 if p.lattice == D2Q9 else 19
+    return {D2Q9: 9, D3Q19: 19, D3Q27: 27}[p.lattice]
 
 
 def _N(p):

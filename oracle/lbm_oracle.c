@@ -50,7 +50,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define QMAX 19
+#define QMAX 27
 
 /* ---- lattice tables (standard Gauss-Hermite sets; the paper does not print them) ---- */
 static const int C_D2Q9[9][3] = {
@@ -67,6 +67,19 @@ static const double W_D3Q19[19] = {
     1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0,
     1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 
+/* D3Q27: rest 8/27, six axis links 2/27, twelve edge diagonals 1/54, eight
+ * corner diagonals 1/216 (the lattice of the paper's 3-D cylindrical Couette runs) */
+static const int C_D3Q27[27][3] = {
+    {0, 0, 0},   {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},   {0, -1, 0},  {0, 0, 1},   {0, 0, -1},
+    {1, 1, 0},   {-1, -1, 0}, {1, -1, 0},  {-1, 1, 0},  {1, 0, 1},   {-1, 0, -1}, {1, 0, -1},
+    {-1, 0, 1},  {0, 1, 1},   {0, -1, -1}, {0, 1, -1},  {0, -1, 1},  {1, 1, 1},   {-1, -1, -1},
+    {1, 1, -1},  {-1, -1, 1}, {1, -1, 1},  {-1, 1, -1}, {-1, 1, 1},  {1, -1, -1}};
+static const double W_D3Q27[27] = {
+    8.0 / 27.0,  2.0 / 27.0,  2.0 / 27.0,  2.0 / 27.0,  2.0 / 27.0,  2.0 / 27.0,  2.0 / 27.0,
+    1.0 / 54.0,  1.0 / 54.0,  1.0 / 54.0,  1.0 / 54.0,  1.0 / 54.0,  1.0 / 54.0,  1.0 / 54.0,
+    1.0 / 54.0,  1.0 / 54.0,  1.0 / 54.0,  1.0 / 54.0,  1.0 / 54.0,  1.0 / 216.0, 1.0 / 216.0,
+    1.0 / 216.0, 1.0 / 216.0, 1.0 / 216.0, 1.0 / 216.0, 1.0 / 216.0, 1.0 / 216.0};
+
 static const double CS2 = 1.0 / 3.0; /* lattice speed of sound squared */
 
 typedef struct {
@@ -81,6 +94,7 @@ static int lat_load(int lattice, lat_t *L) {
   const double *w;
   if (lattice == OR_D2Q9) { L->Q = 9; L->D = 2; c = C_D2Q9; w = W_D2Q9; }
   else if (lattice == OR_D3Q19) { L->Q = 19; L->D = 3; c = C_D3Q19; w = W_D3Q19; }
+  else if (lattice == OR_D3Q27) { L->Q = 27; L->D = 3; c = C_D3Q27; w = W_D3Q27; }
   else return -1;
   for (int i = 0; i < L->Q; ++i) {
     for (int d = 0; d < 3; ++d) L->c[i][d] = c[i][d];

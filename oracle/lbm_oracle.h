@@ -23,7 +23,7 @@
 extern "C" {
 #endif
 
-enum { OR_D2Q9 = 0, OR_D3Q19 = 1 };
+enum { OR_D2Q9 = 0, OR_D3Q19 = 1, OR_D3Q27 = 2 };
 enum { OR_FLUID = 0, OR_SOLID = 1, OR_OPEN = 2 };
 /* Boundary schemes: ELIBB fragmented linear / quadratic (Sec. II.E),
  * linear Bouzidi-Firdaouss-Lallemand (Eq. bfl), half-way bounce-back,

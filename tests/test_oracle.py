@@ -26,7 +26,8 @@ def _read_lattice(name):
 
 
 # ---------------------------------------------------------------- lattice tables
-@pytest.mark.parametrize("lat,name", [(oracle.D2Q9, "d2q9.txt"), (oracle.D3Q19, "d3q19.txt")])
+@pytest.mark.parametrize("lat,name", [(oracle.D2Q9, "d2q9.txt"), (oracle.D3Q19, "d3q19.txt"),
+                                      (oracle.D3Q27, "d3q27.txt")])
 def test_lattice_matches_textbook(oracle_lib, lat, name):
     c, w, opp = oracle.lattice(lat)
     gold = {cv: wv for cv, wv in _read_lattice(name)}
@@ -36,7 +37,7 @@ def test_lattice_matches_textbook(oracle_lib, lat, name):
         assert (c[opp[i]] == -c[i]).all()
 
 
-@pytest.mark.parametrize("lat", [oracle.D2Q9, oracle.D3Q19])
+@pytest.mark.parametrize("lat", [oracle.D2Q9, oracle.D3Q19, oracle.D3Q27])
 def test_lattice_isotropy(oracle_lib, lat):
     """Moments of the weights: sum w = 1, sum w c_a c_b = cs2 delta, 4th-order isotropy."""
     c, w, _ = oracle.lattice(lat)
@@ -53,10 +54,10 @@ def test_lattice_isotropy(oracle_lib, lat):
     np.testing.assert_allclose(np.einsum("i,ia,ib,ic,id->abcd", w, c, c, c, c), iso, atol=1e-16)
 
 
-@pytest.mark.parametrize("lat", [oracle.D2Q9, oracle.D3Q19])
+@pytest.mark.parametrize("lat", [oracle.D2Q9, oracle.D3Q19, oracle.D3Q27])
 def test_equilibrium_moments(oracle_lib, lat):
     """Eq. Eq2ndOrder: sum f^eq = rho, sum c f^eq = rho u, sum c c f^eq = rho (cs2 I + u u)."""
-    Qn = 9 if lat == oracle.D2Q9 else 19
+    Qn = {oracle.D2Q9: 9, oracle.D3Q19: 19, oracle.D3Q27: 27}[lat]
     D = 2 if lat == oracle.D2Q9 else 3
     rng = np.random.default_rng(1)
     n = 7
@@ -137,9 +138,9 @@ def test_fq_equals_uq_below_half_and_cutoff(oracle_lib):
 
 # ---------------------------------------------------------------- bulk invariants
 def _random_state(p, rng, amp=0.05):
-    Qn = 9 if p.lattice == oracle.D2Q9 else 19
     N = p.nx * p.ny * p.nz
     _, w, _ = oracle.lattice(p.lattice)
+    Qn = len(w)
     return w[None, :] * (1.0 + amp * rng.standard_normal((N, Qn)))
 
 
@@ -156,7 +157,8 @@ def _shifted_neighbour(p, x, y, z, c):
 
 
 @pytest.mark.parametrize("lat,dims,xshift", [(oracle.D2Q9, (6, 5, 1), 2), (oracle.D2Q9, (5, 7, 1), 0),
-                                             (oracle.D3Q19, (4, 5, 3), 0), (oracle.D3Q19, (3, 4, 5), 1)])
+                                             (oracle.D3Q19, (4, 5, 3), 0), (oracle.D3Q19, (3, 4, 5), 1),
+                                             (oracle.D3Q27, (4, 3, 5), 1)])
 def test_streaming_is_exact_permutation(oracle_lib, lat, dims, xshift):
     """A local-equilibrium state is a fixed point of BGK collision, so one update is pure
     streaming f_i(x + c_i) = f_i(x) (Eq. LBE), here on the sheared-periodic lattice."""
@@ -178,12 +180,13 @@ def test_streaming_is_exact_permutation(oracle_lib, lat, dims, xshift):
             assert abs(fo[m, i] - f[n, i]) < 1e-15
 
 
-@pytest.mark.parametrize("lat,dims", [(oracle.D2Q9, (8, 6, 1)), (oracle.D3Q19, (5, 4, 6))])
+@pytest.mark.parametrize("lat,dims", [(oracle.D2Q9, (8, 6, 1)), (oracle.D3Q19, (5, 4, 6)),
+                                      (oracle.D3Q27, (4, 5, 3))])
 def test_mass_and_momentum_balance(oracle_lib, lat, dims):
     """Periodic box: collision and streaming conserve mass; with Guo forcing every fluid
     node gains exactly F of momentum per step."""
     rng = np.random.default_rng(5)
-    F = np.array([2e-5, -1e-5, 3e-5 if lat == oracle.D3Q19 else 0.0])
+    F = np.array([2e-5, -1e-5, 0.0 if lat == oracle.D2Q9 else 3e-5])
     p = oracle.params(lat, dims, 0.9, force=F)
     N = p.nx * p.ny * p.nz
     flags = np.zeros(N, np.uint8)
@@ -219,7 +222,7 @@ def _plane_couette(lat, bc, qb, qt, H=16, tau=0.8, U=1e-3, steps=None, impulsive
     return p, s
 
 
-@pytest.mark.parametrize("lat", [oracle.D2Q9, oracle.D3Q19])
+@pytest.mark.parametrize("lat", [oracle.D2Q9, oracle.D3Q19, oracle.D3Q27])
 @pytest.mark.parametrize("bc", [oracle.BC_ELIBB_F, oracle.BC_ELIBB_FQ, oracle.BC_BFL])
 @pytest.mark.parametrize("qb,qt", [(0.3, 0.7), (0.1, 0.9), (0.6, 0.05)])
 def test_steady_plane_couette_exact(oracle_lib, lat, bc, qb, qt):

@@ -8,8 +8,9 @@ properties that do not restate the formula:
 - a non-hydrodynamic (odd, zero-stress) non-equilibrium is projected out: the
   wall value is the equilibrium part alone;
 - with it, the second-order rules still carry steady plane Couette flow at any
-  q: exactly on D2Q9, and up to an O(U^2) Mach effect on D3Q19, which lacks part
-  of the third-order Hermite set; circular Couette flow converges at second order.
+  q: exactly on D2Q9 and D3Q27, and up to an O(U^2) Mach effect on D3Q19, which
+  lacks part of the third-order Hermite set; circular Couette flow converges at
+  second order.
 """
 import numpy as np
 import pytest
@@ -97,10 +98,11 @@ def _couette_error(lat, bc, qb, qt, U, H=16, tau=0.8):
 @pytest.mark.parametrize("bc", [oracle.BC_ELIBB_F, oracle.BC_ELIBB_FQ, oracle.BC_ELIBB_UQ])
 @pytest.mark.parametrize("qb,qt", [(0.3, 0.7), (0.6, 0.05)])
 def test_regularized_steady_plane_couette(oracle_lib, bc, qb, qt):
-    """D2Q9 supports the third-order Hermite terms the estimate uses: the linear
-    profile is exact. D3Q19 lacks part of them: the profile is exact up to a Mach
-    number effect, a relative error that grows exactly as U^2."""
+    """D2Q9 and D3Q27 support the third-order Hermite terms the estimate uses: the
+    linear profile is exact. D3Q19 lacks part of them: the profile is exact up to a
+    Mach number effect, a relative error that grows exactly as U^2."""
     assert _couette_error(oracle.D2Q9, bc, qb, qt, 1e-3) < 1e-10
+    assert _couette_error(oracle.D3Q27, bc, qb, qt, 1e-3) < 1e-10
     e1 = _couette_error(oracle.D3Q19, bc, qb, qt, 1e-3)
     e2 = _couette_error(oracle.D3Q19, bc, qb, qt, 2e-3)
     assert e1 < 1e-7 and abs(e2 / e1 - 4.0) < 0.05, (e1, e2)

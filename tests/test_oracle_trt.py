@@ -62,10 +62,11 @@ def test_trt_relaxes_even_and_odd_modes_at_their_rates(oracle_lib, tau, magic):
     assert np.abs(fo - expect).max() < 1e-15
 
 
-@pytest.mark.parametrize("lat,dims", [(oracle.D2Q9, (8, 6, 1)), (oracle.D3Q19, (5, 4, 6))])
+@pytest.mark.parametrize("lat,dims", [(oracle.D2Q9, (8, 6, 1)), (oracle.D3Q19, (5, 4, 6)),
+                                      (oracle.D3Q27, (4, 5, 3))])
 def test_trt_mass_and_momentum_balance(oracle_lib, lat, dims):
     rng = np.random.default_rng(6)
-    F = np.array([2e-5, -1e-5, 3e-5 if lat == oracle.D3Q19 else 0.0])
+    F = np.array([2e-5, -1e-5, 0.0 if lat == oracle.D2Q9 else 3e-5])
     p = oracle.params(lat, dims, 0.9, force=F, collision=oracle.COLL_TRT, magic=3.0 / 16.0)
     N = p.nx * p.ny * p.nz
     flags = np.zeros(N, np.uint8)
