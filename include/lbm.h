@@ -41,7 +41,7 @@ extern "C" {
 
 typedef struct lbm_sim *lbm_handle;
 
-enum lbm_lattice { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };
+enum lbm_lattice { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2 };
 
 /* Storage type of the populations. F64 computes in FP64. The others keep the
  * shifted value f_i - w_i rho0 in the stated format and compute in FP32. */

@@ -30,7 +30,7 @@ COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC", "--exp
 # per-file extra flags: the geometry kernels round like the plain FP64 definitions
 EXTRA = {"geometry.cu": ["-fmad=false"]}
 # step_inst.cu: one object per (lattice, storage type)
-STEP_INSTANCES = [(lat, sto) for lat in ("D2Q9", "D3Q19") for sto in ("double", "float", "__half", "__nv_bfloat16")]
+STEP_INSTANCES = [(lat, sto) for lat in ("D2Q9", "D3Q19", "D3Q27") for sto in ("double", "float", "__half", "__nv_bfloat16")]
 
 
 def _nvcc():

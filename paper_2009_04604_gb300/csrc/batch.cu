@@ -92,6 +92,14 @@ static cudaError_t batch_launch(const lbm_batch_s *b, int parity) {
       default: return batch_launch_t<D2Q9, __nv_bfloat16, float>(b, parity);
     }
   }
+  if (b->lattice == LBM_D3Q27) {
+    switch (b->dtype) {
+      case LBM_F64: return batch_launch_t<D3Q27, double, double>(b, parity);
+      case LBM_F32: return batch_launch_t<D3Q27, float, float>(b, parity);
+      case LBM_F16: return batch_launch_t<D3Q27, __half, float>(b, parity);
+      default: return batch_launch_t<D3Q27, __nv_bfloat16, float>(b, parity);
+    }
+  }
   switch (b->dtype) {
     case LBM_F64: return batch_launch_t<D3Q19, double, double>(b, parity);
     case LBM_F32: return batch_launch_t<D3Q19, float, float>(b, parity);
@@ -234,6 +242,8 @@ extern "C" int lbm_batch_set_launch(lbm_batch b, int bx, int by, int variant, in
   if (bx < 32 || bx % 32 || by < 1 || bx * by > 256 || variant < 0 || variant > 3 || tiles < 1 || tiles > 4)
     return bfail(b, LBM_ERR_ARG, "invalid launch configuration");
   if (b->dtype == LBM_F64 && variant != 0) return bfail(b, LBM_ERR_ARG, "FP64 takes variant 0 only");
+  if (b->dtype == LBM_F64 && b->lattice == LBM_D3Q27 && bx * by > 128)
+    return bfail(b, LBM_ERR_ARG, "FP64 on D3Q27 takes at most 128 threads per block (shared staging)");
   for (lbm_sim *s : b->sims)
     if (s->nxp % bx) return bfail(b, LBM_ERR_ARG, "bx must divide the padded row length of every simulation");
   b->bx = bx; b->by = by; b->variant = variant; b->T = tiles;
@@ -284,7 +294,8 @@ extern "C" int lbm_batch_autotune(lbm_batch b, int steps, int *bx, int *by, int 
   int rc = LBM_OK;
   const int nvar = b->dtype == LBM_F64 ? 1 : 4;
   const int topts[3] = {1, 2, 4};
-  for (int threads = 128; threads <= 256 && rc == LBM_OK; threads *= 2)
+  const int max_threads = (b->dtype == LBM_F64 && b->lattice == LBM_D3Q27) ? 128 : 256;  // shared staging
+  for (int threads = 128; threads <= max_threads && rc == LBM_OK; threads *= 2)
     for (int bxx = 32; bxx <= threads && rc == LBM_OK; bxx *= 2) {
       bool ok = true;
       for (lbm_sim *s : b->sims) ok = ok && (s->nxp % bxx == 0);

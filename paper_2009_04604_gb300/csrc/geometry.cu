@@ -457,7 +457,8 @@ extern "C" int lbm_build_geometry(lbm_handle h, const uint8_t *base, const doubl
     const unsigned blocks = (unsigned)((h->np + 255) / 256);
     k_geo_flags<<<blocks, 256, 0, st>>>(g, h->flags);
     if (h->lattice == LBM_D2Q9) k_geo_count<D2Q9><<<blocks, 256, 0, st>>>(g, h->flags, crec, clink);
-    else k_geo_count<D3Q19><<<blocks, 256, 0, st>>>(g, h->flags, crec, clink);
+    else if (h->lattice == LBM_D3Q19) k_geo_count<D3Q19><<<blocks, 256, 0, st>>>(g, h->flags, crec, clink);
+    else k_geo_count<D3Q27><<<blocks, 256, 0, st>>>(g, h->flags, crec, clink);
     GEO_CUDA(cudaGetLastError());
     exclusive_scan(crec, nchunk, tot, totals, st);
     exclusive_scan(clink, nchunk, tot, totals + 1, st);
@@ -488,9 +489,12 @@ extern "C" int lbm_build_geometry(lbm_handle h, const uint8_t *base, const doubl
       if (h->lattice == LBM_D2Q9) {
         if (ls == 8) k_geo_fill<D2Q9, double><<<blocks, 256, 0, st>>>(g, crec, clink, h->rec, h->rnode, (double *)h->lq, (double *)h->luw, (double *)h->luw1, h->ltag);
         else k_geo_fill<D2Q9, float><<<blocks, 256, 0, st>>>(g, crec, clink, h->rec, h->rnode, (float *)h->lq, (float *)h->luw, (float *)h->luw1, h->ltag);
-      } else {
+      } else if (h->lattice == LBM_D3Q19) {
         if (ls == 8) k_geo_fill<D3Q19, double><<<blocks, 256, 0, st>>>(g, crec, clink, h->rec, h->rnode, (double *)h->lq, (double *)h->luw, (double *)h->luw1, h->ltag);
         else k_geo_fill<D3Q19, float><<<blocks, 256, 0, st>>>(g, crec, clink, h->rec, h->rnode, (float *)h->lq, (float *)h->luw, (float *)h->luw1, h->ltag);
+      } else {
+        if (ls == 8) k_geo_fill<D3Q27, double><<<blocks, 256, 0, st>>>(g, crec, clink, h->rec, h->rnode, (double *)h->lq, (double *)h->luw, (double *)h->luw1, h->ltag);
+        else k_geo_fill<D3Q27, float><<<blocks, 256, 0, st>>>(g, crec, clink, h->rec, h->rnode, (float *)h->lq, (float *)h->luw, (float *)h->luw1, h->ltag);
       }
       GEO_CUDA(cudaGetLastError());
     }
@@ -692,6 +696,14 @@ static cudaError_t move_dispatch(int lattice, int dtype, Fn &&fn) {
       case 1: return fn.template operator()<D2Q9, float, float>();
       case 2: return fn.template operator()<D2Q9, __half, float>();
       default: return fn.template operator()<D2Q9, __nv_bfloat16, float>();
+    }
+  }
+  if (lattice == 2) {
+    switch (dtype) {
+      case 0: return fn.template operator()<D3Q27, double, double>();
+      case 1: return fn.template operator()<D3Q27, float, float>();
+      case 2: return fn.template operator()<D3Q27, __half, float>();
+      default: return fn.template operator()<D3Q27, __nv_bfloat16, float>();
     }
   }
   switch (dtype) {

@@ -45,6 +45,13 @@ static cudaError_t dispatch(int lattice, int dtype, Fn &&fn) {
       case 2: return fn.template operator()<D3Q19, __half, float>();
       case 3: return fn.template operator()<D3Q19, __nv_bfloat16, float>();
     }
+  } else if (lattice == 2) {
+    switch (dtype) {
+      case 0: return fn.template operator()<D3Q27, double, double>();
+      case 1: return fn.template operator()<D3Q27, float, float>();
+      case 2: return fn.template operator()<D3Q27, __half, float>();
+      case 3: return fn.template operator()<D3Q27, __nv_bfloat16, float>();
+    }
   }
   return cudaErrorInvalidValue;
 }

@@ -686,7 +686,7 @@ __device__ __forceinline__ void boundary_tile(const View &v, const S *__restrict
   const Rec r = rs.rec[rid];
   const int n = (int)rs.rnode[rid];
   const int x = n % v.nxp, y = (n / v.nxp) % v.ny, z = n / (v.nxp * v.ny);
-  boundary_node<L, S, M>(v, rs, r, fin, fout, n, x, y, z, stage + t, 256);
+  boundary_node<L, S, M>(v, rs, r, fin, fout, n, x, y, z, stage + t, stage_threads<L, M>());
 }
 
 // Block b takes table entries b*T .. b*T+T-1 (T = v.tpb_tiles <= 4), whose
@@ -694,7 +694,7 @@ __device__ __forceinline__ void boundary_tile(const View &v, const S *__restrict
 template <class L, typename S, typename M, int MINB, int PHYS, bool PAIR = false>
 __global__ void __launch_bounds__(256, MINB) k_step(const View v, const S *__restrict__ fin,
                                                     S *__restrict__ fout) {
-  __shared__ M stage[L::Q * 256];  // boundary tiles: populations, [direction][thread]
+  __shared__ M stage[L::Q * stage_threads<L, M>()];  // boundary tiles: populations, [direction][thread]
   const int T = v.tpb_tiles;
   const int first = blockIdx.x * T;
   int2 tl[4];
@@ -923,7 +923,7 @@ template <class L, typename S, typename M, int MINB, int PHYS>
 __global__ void __launch_bounds__(256, MINB) k_step_batch(const BatchEntry *__restrict__ entries,
                                                           const int4 *__restrict__ tiles, int ntiles,
                                                           int T, int parity) {
-  __shared__ M stage[L::Q * 256];
+  __shared__ M stage[L::Q * stage_threads<L, M>()];
   __shared__ BatchEntry se;
   const int t = threadIdx.y * blockDim.x + threadIdx.x;
   for (int k = 0; k < T; ++k) {

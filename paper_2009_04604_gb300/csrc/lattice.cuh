@@ -3,8 +3,8 @@
 //
 // Directions are ordered lexicographically by (c_z, c_y, c_x). With that order the
 // opposite of direction i is Q-1-i and the rest population sits in the middle.
-// Weights are the standard Gauss-Hermite weights of the D2Q9 / D3Q19 sets
-// (Sec. II.A, c_s^2 = 1/3): 4/9, 1/9, 1/36 and 1/3, 1/18, 1/36.
+// Weights are the standard Gauss-Hermite weights of the D2Q9 / D3Q19 / D3Q27 sets
+// (Sec. II.A, c_s^2 = 1/3): 4/9, 1/9, 1/36; 1/3, 1/18, 1/36; 8/27, 2/27, 1/54, 1/216.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -39,6 +39,16 @@ struct D3Q19 {
   }
 };
 
+// all 27 velocities with components in {-1, 0, 1} (the lattice of the paper's 3-D
+// cylindrical Couette runs): i = 9 (c_z + 1) + 3 (c_y + 1) + (c_x + 1)
+struct D3Q27 {
+  static constexpr int Q = 27;
+  static constexpr int D = 3;
+  __host__ __device__ static constexpr int cx(int i) { return i % 3 - 1; }
+  __host__ __device__ static constexpr int cy(int i) { return (i / 3) % 3 - 1; }
+  __host__ __device__ static constexpr int cz(int i) { return i / 9 - 1; }
+};
+
 template <class L>
 __host__ __device__ constexpr int c2(int i) {
   return L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i);
@@ -47,12 +57,22 @@ __host__ __device__ constexpr int c2(int i) {
 // Gauss-Hermite weight of direction i, from |c_i|^2.
 template <class L>
 __host__ __device__ constexpr double weight(int i) {
-  return L::Q == 9 ? (c2<L>(i) == 0 ? 4.0 / 9.0 : (c2<L>(i) == 1 ? 1.0 / 9.0 : 1.0 / 36.0))
-                   : (c2<L>(i) == 0 ? 1.0 / 3.0 : (c2<L>(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0));
+  return L::Q == 9    ? (c2<L>(i) == 0 ? 4.0 / 9.0 : (c2<L>(i) == 1 ? 1.0 / 9.0 : 1.0 / 36.0))
+         : L::Q == 19 ? (c2<L>(i) == 0 ? 1.0 / 3.0 : (c2<L>(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0))
+                      : (c2<L>(i) == 0 ? 8.0 / 27.0
+                                       : (c2<L>(i) == 1 ? 2.0 / 27.0 : (c2<L>(i) == 2 ? 1.0 / 54.0 : 1.0 / 216.0)));
 }
 
 template <class L>
 __host__ __device__ constexpr int opp(int i) { return L::Q - 1 - i; }
+
+// Threads per block whose boundary work the step kernels stage in static shared
+// memory: 256, or 128 where Q x 256 values of the math type would pass the 48 KB
+// static limit (FP64 on D3Q27). Launches are limited to that many threads.
+template <class L, typename M>
+__host__ __device__ constexpr int stage_threads() {
+  return L::Q * 256 * (int)sizeof(M) <= 48 * 1024 ? 256 : 128;
+}
 
 // Run-time direction index: the velocity components packed as 2-bit fields
 // (component + 1) in 64-bit constants, and the weight in the math type. These
@@ -77,9 +97,10 @@ __device__ __forceinline__ M dweight(int i) {
   const int a = dcx<L>(i), b = dcy<L>(i), c = dcz<L>(i);
   const int k = a * a + b * b + c * c;
   constexpr M w0 = M(weight<L>(L::Q / 2));  // rest
-  constexpr M w1 = M(L::Q == 9 ? 1.0 / 9.0 : 1.0 / 18.0);
-  constexpr M w2 = M(1.0 / 36.0);
-  return k == 0 ? w0 : (k == 1 ? w1 : w2);
+  constexpr M w1 = M(L::Q == 9 ? 1.0 / 9.0 : (L::Q == 19 ? 1.0 / 18.0 : 2.0 / 27.0));
+  constexpr M w2 = M(L::Q == 27 ? 1.0 / 54.0 : 1.0 / 36.0);
+  constexpr M w3 = M(1.0 / 216.0);  // D3Q27 corners
+  return k == 0 ? w0 : (k == 1 ? w1 : (k == 2 ? w2 : w3));
 }
 
 // ---- storage <-> math conversions (round to nearest even on store) ----
@@ -146,7 +167,7 @@ struct View {
   // per-direction element offsets, computed on the host so that the kernels use
   // them as constant operands: soff[i] = i np (plane i), loff[i] = i np - (c_ix +
   // c_iy nxp + c_iz nxp ny) (the source of population i at an interior node)
-  int soff[19], loff[19];
+  int soff[27], loff[27];
   int ntiles, tpb_tiles;     // table length; consecutive table entries per block
   // moving body: records of the nodes of its region, rebuilt every step
   RecSet dyn;

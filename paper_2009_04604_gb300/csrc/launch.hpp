@@ -21,7 +21,7 @@ struct Launch {
 cudaError_t prepare_step_tma(int lattice, int dtype, int phys, int bx, int by, long long ntiles,
                              int *blocks, int *smem);
 
-// lattice: 0 D2Q9, 1 D3Q19; dtype: 0 F64, 1 F32, 2 F16, 3 BF16
+// lattice: 0 D2Q9, 1 D3Q19, 2 D3Q27; dtype: 0 F64, 1 F32, 2 F16, 3 BF16
 // variant: register budget of the step kernel, at least variant+1 resident
 // 256-thread blocks per SM (0..3), 4: the TMA-staged persistent kernel, or 5..7:
 // two nodes per thread with at least 1..3 resident blocks per SM (FP32/FP16/BF16).

@@ -48,16 +48,18 @@ static void fill_info(int *c, double *w) {
 extern "C" int lbm_lattice_info(int lattice, int *Q, int *c, double *w) {
   if (lattice == LBM_D2Q9) { if (Q) *Q = 9; fill_info<D2Q9>(c, w); return LBM_OK; }
   if (lattice == LBM_D3Q19) { if (Q) *Q = 19; fill_info<D3Q19>(c, w); return LBM_OK; }
+  if (lattice == LBM_D3Q27) { if (Q) *Q = 27; fill_info<D3Q27>(c, w); return LBM_OK; }
   return lbm_fail(nullptr, LBM_ERR_ARG, "unknown lattice");
 }
 
 void lbm_sim::lattice_c(int i, int &x, int &y, int &z) const {
   if (lattice == LBM_D2Q9) { x = D2Q9::cx(i); y = D2Q9::cy(i); z = 0; }
-  else { x = D3Q19::cx(i); y = D3Q19::cy(i); z = D3Q19::cz(i); }
+  else if (lattice == LBM_D3Q19) { x = D3Q19::cx(i); y = D3Q19::cy(i); z = D3Q19::cz(i); }
+  else { x = D3Q27::cx(i); y = D3Q27::cy(i); z = D3Q27::cz(i); }
 }
 
 double lbm_sim::lattice_w(int i) const {
-  return lattice == LBM_D2Q9 ? weight<D2Q9>(i) : weight<D3Q19>(i);
+  return lattice == LBM_D2Q9 ? weight<D2Q9>(i) : (lattice == LBM_D3Q19 ? weight<D3Q19>(i) : weight<D3Q27>(i));
 }
 
 size_t lbm_sim::elem_size() const {
@@ -71,19 +73,20 @@ extern "C" int lbm_create(int lattice, const int dims[3], double tau, int dtype,
                           lbm_handle *out) {
   if (!out || !dims) return lbm_fail(nullptr, LBM_ERR_ARG, "null argument");
   *out = nullptr;
-  if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19) return lbm_fail(nullptr, LBM_ERR_ARG, "unknown lattice");
+  if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19 && lattice != LBM_D3Q27)
+    return lbm_fail(nullptr, LBM_ERR_ARG, "unknown lattice");
   if (dtype < LBM_F64 || dtype > LBM_BF16) return lbm_fail(nullptr, LBM_ERR_ARG, "unknown dtype");
   if (!(tau > 0.5)) return lbm_fail(nullptr, LBM_ERR_ARG, "tau must exceed 1/2");
   if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1) return lbm_fail(nullptr, LBM_ERR_ARG, "dims must be positive");
   if (lattice == LBM_D2Q9 && dims[2] != 1) return lbm_fail(nullptr, LBM_ERR_ARG, "D2Q9 needs nz = 1");
   const long long nxp = (dims[0] + 31) / 32 * 32;
   const long long np = nxp * dims[1] * (long long)dims[2];
-  const long long Qn = lattice == LBM_D2Q9 ? 9 : 19;
+  const long long Qn = lattice == LBM_D2Q9 ? 9 : (lattice == LBM_D3Q19 ? 19 : 27);
   if (np * Qn >= (1LL << 31))
     return lbm_fail(nullptr, LBM_ERR_ARG, "grid too large: Q x padded nodes must stay below 2^31");
   lbm_sim *h = new lbm_sim();
   h->lattice = lattice;
-  h->Q = lattice == LBM_D2Q9 ? 9 : 19;
+  h->Q = (int)Qn;
   h->dtype = dtype;
   h->nx = dims[0]; h->ny = dims[1]; h->nz = dims[2];
   h->nxp = (int)nxp;
@@ -271,7 +274,8 @@ void lbm_sim::tune_default() {
   int bx = 32;
   while (bx < 128 && nxp % (bx * 2) == 0) bx *= 2;
   step_bx = bx;
-  step_by = std::max(1, 256 / bx);
+  const int threads = (dtype == LBM_F64 && lattice == LBM_D3Q27) ? 128 : 256;  // shared staging
+  step_by = std::max(1, threads / bx);
 }
 
 Launch lbm_sim::step_shape() const {
@@ -345,7 +349,7 @@ extern "C" int lbm_init(lbm_handle h, double rho, const double u[3]) {
   if (!h) return lbm_fail(nullptr, LBM_ERR_ARG, "null handle");
   if (!h->geom_ok) return lbm_fail(h, LBM_ERR_STATE, "set the geometry first");
   if (!(rho > 0.0)) return lbm_fail(h, LBM_ERR_ARG, "rho must be positive");
-  double ux = u ? u[0] : 0.0, uy = u ? u[1] : 0.0, uz = (u && h->lattice == LBM_D3Q19) ? u[2] : 0.0;
+  double ux = u ? u[0] : 0.0, uy = u ? u[1] : 0.0, uz = (u && h->lattice != LBM_D2Q9) ? u[2] : 0.0;
   LBM_CUDA(h, launch_init(h->lattice, h->dtype, h->view(), h->f[h->cur], rho, ux, uy, uz, h->aux_shape()));
   h->state_ok = true;
   return LBM_OK;
@@ -596,6 +600,7 @@ static bool valid_launch(const lbm_sim *h, int bx, int by, int variant, int tile
   if (bx < 32 || bx % 32 || h->nxp % bx || by < 1 || bx * by > 256) return false;
   if (variant < 0 || variant > 7 || tiles < 1 || tiles > 4) return false;
   if (h->dtype == LBM_F64 && variant != 0) return false;
+  if (h->dtype == LBM_F64 && h->lattice == LBM_D3Q27 && bx * by > 128) return false;  // shared staging
   if (variant >= 5 && (h->nxp % (2 * bx) || h->bc == LBM_BC_BFL)) return false;  // pairs: whole rows, no BFL
   return true;
 }

@@ -133,7 +133,8 @@ cudaError_t prepare_step_tma_ls(int phys, int bx, int by, long long ntiles, int 
 
 #define LBM_STEP_INSTANCES(X) \
   X(D2Q9, double) X(D2Q9, float) X(D2Q9, __half) X(D2Q9, __nv_bfloat16) \
-  X(D3Q19, double) X(D3Q19, float) X(D3Q19, __half) X(D3Q19, __nv_bfloat16)
+  X(D3Q19, double) X(D3Q19, float) X(D3Q19, __half) X(D3Q19, __nv_bfloat16) \
+  X(D3Q27, double) X(D3Q27, float) X(D3Q27, __half) X(D3Q27, __nv_bfloat16)
 
 #define LBM_STEP_DECLARE(Lat, Sto)                                                                  \
   extern template cudaError_t launch_step_ls<Lat, Sto>(int, const View &, const void *, void *,    \

@@ -1,6 +1,6 @@
 // step_inst.cu -- explicit instantiation of the fused step for one lattice and
 // storage type. The build compiles this file once per pair, with
-// -DLBM_STEP_LATTICE=<D2Q9|D3Q19> -DLBM_STEP_STORE=<double|float|__half|__nv_bfloat16>;
+// -DLBM_STEP_LATTICE=<D2Q9|D3Q19|D3Q27> -DLBM_STEP_STORE=<double|float|__half|__nv_bfloat16>;
 // without them it defines nothing.
 #include "step.cuh"
 

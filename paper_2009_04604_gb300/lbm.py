@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "lbm.h")
 
-D2Q9, D3Q19 = 0, 1
+D2Q9, D3Q19, D3Q27 = 0, 1, 2
 F64, F32, F16, BF16 = 0, 1, 2, 3
 BC_ELIBB_F, BC_ELIBB_FQ, BC_BFL, BC_HWBB, BC_ELIBB_U, BC_ELIBB_UQ = 0, 1, 2, 3, 4, 5
 COLL_BGK, COLL_TRT = 0, 1
@@ -122,8 +122,8 @@ def lattice_info(lattice):
     """``(c[Q,3], w[Q])`` in the library's direction order."""
     lib = load()
     Q = ctypes.c_int()
-    c = np.zeros((19, 3), np.int32)
-    w = np.zeros(19)
+    c = np.zeros((27, 3), np.int32)
+    w = np.zeros(27)
     _check(lib.lbm_lattice_info(lattice, ctypes.byref(Q), _np_ptr(c, ctypes.c_int), _np_ptr(w, ctypes.c_double)))
     return c[:Q.value].copy(), w[:Q.value].copy()
 
@@ -162,7 +162,7 @@ class Simulation:
         self._torch = torch
         self.lib = load()
         self.lattice = lattice
-        self.Q = 9 if lattice == D2Q9 else 19
+        self.Q = {D2Q9: 9, D3Q19: 19, D3Q27: 27}[lattice]
         dims = list(dims) + [1] * (3 - len(dims))
         self.dims = tuple(int(d) for d in dims)
         self.N = self.dims[0] * self.dims[1] * self.dims[2]

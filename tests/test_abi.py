@@ -39,7 +39,8 @@ def _golden(name):
     return rows
 
 
-@pytest.mark.parametrize("lat,name", [(lbm.D2Q9, "d2q9.txt"), (lbm.D3Q19, "d3q19.txt")])
+@pytest.mark.parametrize("lat,name", [(lbm.D2Q9, "d2q9.txt"), (lbm.D3Q19, "d3q19.txt"),
+                                      (lbm.D3Q27, "d3q27.txt")])
 def test_lattice_tables(lib, lat, name):
     c, w = lbm.lattice_info(lat)
     gold = _golden(name)

@@ -33,7 +33,7 @@ def _make(case, dtype):
         # odd row lengths: the last pair of a row holds one node and one pad
         lat, dims, xshift = ((lbm.D3Q19, (47, 13, 11), 0) if case == "random3d"
                              else (lbm.D2Q9, (61, 19, 1), 7))
-        Q = 9 if lat == lbm.D2Q9 else 19
+        Q = {lbm.D2Q9: 9, lbm.D3Q19: 19, lbm.D3Q27: 27}[lat]
         flags, q, uw, uw1, tag = W.random_geometry(dims, seed=23, Q=Q)
         if lat == lbm.D2Q9:
             uw[..., 2] = 0.0

@@ -33,7 +33,7 @@ BCS = [lbm.BC_ELIBB_F, lbm.BC_ELIBB_FQ, lbm.BC_BFL, lbm.BC_HWBB]
 
 
 def _random_case(lat, dims, seed, xshift=0, force=(0.0, 0.0, 0.0), tau=0.8):
-    Q = 9 if lat == lbm.D2Q9 else 19
+    Q = {lbm.D2Q9: 9, lbm.D3Q19: 19, lbm.D3Q27: 27}[lat]
     N = int(np.prod(dims))
     flags, q, uw, uw1, tag = W.random_geometry(dims, seed=seed, Q=Q)
     if lat == lbm.D2Q9:
@@ -247,7 +247,7 @@ def test_edge_cases():
         wl = dict(lattice=lat, dims=dims, tau=0.9, xshift=0, force=(1e-5, 0, 0), rho0=1.0)
         N = int(np.prod(dims))
         flags = np.zeros(N, np.uint8)
-        Q = 9 if lat == lbm.D2Q9 else 19
+        Q = {lbm.D2Q9: 9, lbm.D3Q19: 19, lbm.D3Q27: 27}[lat]
         rho, u, xi = W.random_fields(N, seed=5, Q=Q, two_d=lat == lbm.D2Q9)
         p = oracle_params(wl)
         f = oracle.init_eq(p, flags, rho, u) * (1 + xi)
