@@ -2,7 +2,7 @@
  * lbm.h -- C ABI of the GB300 (sm_103a) lattice Boltzmann library liblbm.so.
  *
  * The library advances the lattice Boltzmann equation with BGK or TRT collision on
- * D2Q9 and D3Q19 lattices (Sec. II.A, Eqs. LBE, LB-BGK, Eq2ndOrder, magic-parameter
+ * D2Q9, D3Q19 and D3Q27 lattices (Sec. II.A, Eqs. LBE, LB-BGK, Eq2ndOrder, magic-parameter
  * of arXiv:2009.04604) in one fused stream-collide kernel. On boundary nodes the
  * same kernel applies a link-wise curved-wall Dirichlet rule. The rules are ELIBB-F,
  * -FQ, -U and -UQ (Sec. II.D), linear BFL (Sec. II.B, Eq. bfl) and half-way bounce-back,
