@@ -99,8 +99,12 @@ __device__ __forceinline__ M dweight(int i) {
   constexpr M w0 = M(weight<L>(L::Q / 2));  // rest
   constexpr M w1 = M(L::Q == 9 ? 1.0 / 9.0 : (L::Q == 19 ? 1.0 / 18.0 : 2.0 / 27.0));
   constexpr M w2 = M(L::Q == 27 ? 1.0 / 54.0 : 1.0 / 36.0);
-  constexpr M w3 = M(1.0 / 216.0);  // D3Q27 corners
-  return k == 0 ? w0 : (k == 1 ? w1 : (k == 2 ? w2 : w3));
+  if constexpr (L::Q == 27) {  // corners only on D3Q27
+    constexpr M w3 = M(1.0 / 216.0);
+    return k == 0 ? w0 : (k == 1 ? w1 : (k == 2 ? w2 : w3));
+  } else {
+    return k == 0 ? w0 : (k == 1 ? w1 : w2);
+  }
 }
 
 // ---- storage <-> math conversions (round to nearest even on store) ----
