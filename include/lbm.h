@@ -255,13 +255,15 @@ int lbm_get_counts(lbm_handle h, int64_t *n_fluid, int64_t *n_boundary, int64_t 
  *   variant 5..7: two nodes per thread along x, with vector loads and stores,
  *     at least 1..3 resident blocks per SM. A block covers 2*bx nodes of a row,
  *     which must divide the padded row. FP32/FP16/BF16, not with BFL (switching
- *     to BFL moves the launch back to variant 0).
- * FP64 storage accepts variant 0 only;
+ *     to BFL moves the launch back to variant 0);
  *   tiles 1..4: consecutive entries of the step kernel's tile table that one
  *     block processes. The table lists, plane by plane, the lattice tiles and
  *     then the boundary-record tiles.
- * The default is the widest bx <= 128 that divides the row, by = 256/bx,
- * variant 0, tiles 4. */
+ * FP64 storage accepts variant 0 only, and on D3Q27 at most 128 threads per block
+ * (27 x 256 doubles of boundary staging would exceed the static shared memory).
+ * The default is the widest bx <= 128 that divides the row, by = 256/bx (128/bx
+ * for FP64 on D3Q27), variant 0, tiles 4. LBM_ERR_ARG for an invalid
+ * configuration. */
 int lbm_set_launch(lbm_handle h, int bx, int by, int variant, int tiles);
 int lbm_get_launch(lbm_handle h, int *bx, int *by, int *variant, int *tiles);
 
