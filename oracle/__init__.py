@@ -27,7 +27,7 @@ _lib = None
 D2Q9, D3Q19, D3Q27 = 0, 1, 2
 FLUID, SOLID, OPEN = 0, 1, 2
 BC_ELIBB_F, BC_ELIBB_FQ, BC_BFL, BC_HWBB, BC_ELIBB_U, BC_ELIBB_UQ = 0, 1, 2, 3, 4, 5
-SHAPE_SPHERE, SHAPE_SPHERE_OUT, SHAPE_ELLIPSOID, SHAPE_STRIP = 0, 1, 2, 3
+SHAPE_SPHERE, SHAPE_SPHERE_OUT, SHAPE_ELLIPSOID, SHAPE_STRIP, SHAPE_SHELL = 0, 1, 2, 3, 4
 COLL_BGK, COLL_TRT = 0, 1
 NEQ_BOUNCE_BACK, NEQ_REGULARIZED = 0, 1
 
@@ -76,12 +76,12 @@ def _load():
             d, i32, u8 = P(ctypes.c_double), P(ctypes.c_int32), P(ctypes.c_uint8)
             lib.or_lattice.argtypes = [ctypes.c_int, P(ctypes.c_int), d, P(ctypes.c_int)]
             lib.or_init_eq.argtypes = [P(Params), u8, d, d, d]
-            lib.or_step.argtypes = [P(Params), u8, d, d, d, d, d, d]
+            lib.or_step.argtypes = [P(Params), u8, d, u8, d, d, d, d, d]
             lib.or_macros.argtypes = [P(Params), u8, d, d, d]
             lib.or_mass.argtypes = [P(Params), u8, d]
             lib.or_mass.restype = ctypes.c_double
             lib.or_refill.argtypes = [P(Params), u8, u8, d, d]
-            lib.or_geometry.argtypes = [P(Params), u8, d, P(Shape), ctypes.c_int, u8, d, d, d, i32]
+            lib.or_geometry.argtypes = [P(Params), u8, d, P(Shape), ctypes.c_int, u8, d, d, d, i32, u8]
             lib.or_geometry.restype = ctypes.c_long
             lib.or_bc_weights.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, d, d]
             _lib = lib
@@ -146,13 +146,16 @@ def init_eq(p, flags, rho=None, u=None):
     return f
 
 
-def step(p, flags, f, q=None, uw=None, uw1=None, want_force=False):
-    """One update; returns ``fout`` or ``(fout, flink[N,Q,3])``."""
+def step(p, flags, f, q=None, uw=None, uw1=None, want_force=False, shell=None):
+    """One update; returns ``fout`` or ``(fout, flink[N,Q,3])``. ``shell[N,Q]``
+    marks the links that cross a thin shell (1: node outside, 2: inside)."""
     f = _cd(f)
     fout = np.empty_like(f)
     flink = np.zeros((_N(p), _Q(p), 3)) if want_force else None
+    sh = None if shell is None else _c8(shell)
     rc = _load().or_step(ctypes.byref(p), _ptr(_c8(flags), ctypes.c_uint8), _dp(_cd(q)),
-                         _dp(_cd(uw)), _dp(_cd(uw1)), _dp(f), _dp(fout), _dp(flink))
+                         _ptr(sh, ctypes.c_uint8), _dp(_cd(uw)), _dp(_cd(uw1)), _dp(f), _dp(fout),
+                         _dp(flink))
     if rc != 0:
         raise ValueError("or_step rejected its arguments")
     return (fout, flink) if want_force else fout
@@ -191,20 +194,29 @@ def make_shapes(specs):
     return arr
 
 
-def geometry(p, base=None, base_u=None, shapes=()):
-    """Flags and per-link q, u_w(t), u_w(t+1), tag from analytic shapes."""
+def geometry(p, base=None, base_u=None, shapes=(), with_shell=False):
+    """Flags and per-link q, u_w(t), u_w(t+1), tag from analytic shapes; with
+    ``with_shell`` also the thin-shell marks ``shell[N,Q]`` that ``step`` takes.
+    Raises ValueError when a fluid node lies exactly on a thin shell."""
     N, Qn = _N(p), _Q(p)
     flags = np.zeros(N, np.uint8)
     q = np.zeros((N, Qn))
     uw = np.zeros((N, Qn, 3))
     uw1 = np.zeros((N, Qn, 3))
     tag = np.zeros((N, Qn), np.int32)
+    shell = np.zeros((N, Qn), np.uint8)
     arr = make_shapes(list(shapes))
     base = None if base is None else _c8(np.reshape(base, -1))
     base_u = _cd(None if base_u is None else np.reshape(base_u, (-1, 3)))
-    _load().or_geometry(ctypes.byref(p), _ptr(base, ctypes.c_uint8), _dp(base_u), arr, len(shapes),
-                        _ptr(flags, ctypes.c_uint8), _dp(q), _dp(uw), _dp(uw1),
-                        _ptr(tag, ctypes.c_int32))
+    rc = _load().or_geometry(ctypes.byref(p), _ptr(base, ctypes.c_uint8), _dp(base_u), arr,
+                             len(shapes), _ptr(flags, ctypes.c_uint8), _dp(q), _dp(uw), _dp(uw1),
+                             _ptr(tag, ctypes.c_int32), _ptr(shell, ctypes.c_uint8))
+    if rc == -2:
+        raise ValueError("a fluid node lies exactly on a thin shell")
+    if rc < 0:
+        raise ValueError("or_geometry rejected its arguments")
+    if with_shell:
+        return flags, q, uw, uw1, tag, shell
     return flags, q, uw, uw1, tag
 
 
@@ -219,10 +231,11 @@ def bc_weights(bc, q, qcut=0.01):
 class Sim:
     """Small driver holding an oracle state (flags, links, populations)."""
 
-    def __init__(self, p, flags, q=None, uw=None, uw1=None, f=None):
+    def __init__(self, p, flags, q=None, uw=None, uw1=None, f=None, shell=None):
         self.p = p
         self.flags = _c8(np.reshape(flags, -1))
         self.q, self.uw, self.uw1 = q, uw, uw1
+        self.shell = shell
         self.f = init_eq(p, self.flags) if f is None else _cd(f)
         self.t = 0
 
@@ -230,9 +243,10 @@ class Sim:
         flink = None
         for _ in range(n):
             if want_force:
-                self.f, flink = step(self.p, self.flags, self.f, self.q, self.uw, self.uw1, True)
+                self.f, flink = step(self.p, self.flags, self.f, self.q, self.uw, self.uw1, True,
+                                     self.shell)
             else:
-                self.f = step(self.p, self.flags, self.f, self.q, self.uw, self.uw1)
+                self.f = step(self.p, self.flags, self.f, self.q, self.uw, self.uw1, shell=self.shell)
             self.t += 1
         return flink
 

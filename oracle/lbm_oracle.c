@@ -291,8 +291,8 @@ void or_init_eq(const or_params *p, const uint8_t *flags, const double *rho, con
 }
 
 /* ---- one time step ---- */
-int or_step(const or_params *p, const uint8_t *flags, const double *q, const double *uw,
-            const double *uw1, const double *f, double *fout, double *flink) {
+int or_step(const or_params *p, const uint8_t *flags, const double *q, const uint8_t *shell,
+            const double *uw, const double *uw1, const double *f, double *fout, double *flink) {
   lat_t L;
   if (lat_load(p->lattice, &L) || p->tau <= 0.5 || !flags || !f || !fout) return -1;
   const int Q = L.Q;
@@ -327,18 +327,21 @@ int or_step(const or_params *p, const uint8_t *flags, const double *q, const dou
 
   for (long n = 0; n < N * Q; ++n) fout[n] = 0.0;
 
-  /* 2. streaming: f_i(x + c_i, t+1) = f*_i(x, t) between fluid nodes (Eq. LBE) */
+  /* 2. streaming: f_i(x + c_i, t+1) = f*_i(x, t) between fluid nodes (Eq. LBE),
+   * except across a thin shell (link i of x + c_i marked in shell) */
 #pragma omp parallel for schedule(static)
   for (long n = 0; n < N; ++n) {
     if (flags[n] != OR_FLUID) continue;
     int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long)nx * ny));
     for (int i = 0; i < Q; ++i) {
       long m = nbr(p, x, y, z, L.c[i][0], L.c[i][1], L.c[i][2]);
-      if (flags[m] == OR_FLUID) fout[m * Q + i] = fpost[n * Q + i];
+      if (flags[m] == OR_FLUID && !(shell && shell[m * Q + i])) fout[m * Q + i] = fpost[n * Q + i];
     }
   }
 
-  /* 3. boundary rule for every cut link (x_F, i): x_F - c_i is not fluid */
+  /* 3. boundary rule for every cut link (x_F, i): x_F - c_i is not fluid, or lies
+   * across a thin shell. A shell is a wall seen from both of its sides, so each
+   * side applies the rule to the population coming back to it. */
 #pragma omp parallel for schedule(static)
   for (long n = 0; n < N; ++n) {
     if (flags[n] != OR_FLUID) continue;
@@ -356,7 +359,7 @@ int or_step(const or_params *p, const uint8_t *flags, const double *q, const dou
       }
     for (int i = 1; i < Q; ++i) {
       long m = nbr(p, x, y, z, -L.c[i][0], -L.c[i][1], -L.c[i][2]);
-      if (flags[m] == OR_FLUID) continue;
+      if (flags[m] == OR_FLUID && !(shell && shell[n * Q + i])) continue;
       const int ib = L.opp[i];
       /* pre-collision non-equilibrium of the outgoing population (Eq. neqbb-s) */
       const double fneq_ib = f[n * Q + ib] - feq(&L, ib, rF, uF);
@@ -388,9 +391,9 @@ int or_step(const or_params *p, const uint8_t *flags, const double *q, const dou
       const double f0 = feq(&L, i, rF, u1) + fn0;
       const double f1 = feq(&L, i, rF, u0) + post * fn1;
       const double s1 = p->s1_exact ? 1.0 + cu / c2 : 1.0;
-      /* second fluid node along the link (BFL only) */
+      /* second fluid node along the link (BFL only), on the node's side of any shell */
       long ff = nbr(p, x, y, z, L.c[i][0], L.c[i][1], L.c[i][2]);
-      int ff_fluid = flags[ff] == OR_FLUID;
+      int ff_fluid = flags[ff] == OR_FLUID && !(shell && shell[n * Q + ib]);
       int pt[3];
       int np = bc_points(p->bc, qq, p->qcut, ff_fluid, pt);
       double s[3], v[3];
@@ -416,12 +419,14 @@ int or_step(const or_params *p, const uint8_t *flags, const double *q, const dou
     }
   }
   if (flink) {
-    /* links that are not wall links carry no force */
+    /* links that are not wall links carry no force; of a thin shell's links only
+     * those on its outer side count (the fluid inside moves with the body) */
     for (long n = 0; n < N; ++n) {
       int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long)nx * ny));
       for (int i = 0; i < Q; ++i) {
         long m = nbr(p, x, y, z, -L.c[i][0], -L.c[i][1], -L.c[i][2]);
-        int wall = flags[n] == OR_FLUID && i > 0 && flags[m] == OR_SOLID;
+        const int sh = shell ? shell[n * Q + i] : 0;
+        int wall = flags[n] == OR_FLUID && i > 0 && ((flags[m] == OR_SOLID && !sh) || sh == 1);
         if (!wall) for (int a = 0; a < 3; ++a) flink[(n * Q + i) * 3 + a] = 0.0;
       }
     }
@@ -489,7 +494,14 @@ static int shape_solid(const or_shape *s, int D, const double x[3]) {
   }
 }
 
-/* Smallest t in (0,1] where x - t c enters the solid of shape s, or -1.
+/* Inside a thin shell: strictly closer to the centre than r0. */
+static int shell_inside(const or_shape *s, int D, const double x[3]) {
+  double d0 = x[0] - s->c[0], d1 = x[1] - s->c[1], d2 = D == 3 ? x[2] - s->c[2] : 0.0;
+  return d0 * d0 + d1 * d1 + d2 * d2 < s->r[0] * s->r[0];
+}
+
+/* Smallest t in (0,1] where x - t c enters the solid of shape s (or, for a thin
+ * shell, meets its surface), or -1.
  * Quadratic roots use the cancellation-free form (Numerical Recipes, Sec. 5.6). */
 static double shape_cross(const or_shape *s, int D, const double x[3], const int c[3]) {
   double d[3], e[3];
@@ -497,6 +509,7 @@ static double shape_cross(const or_shape *s, int D, const double x[3], const int
   switch (s->type) {
     case OR_SHAPE_SPHERE:
     case OR_SHAPE_SPHERE_OUT:
+    case OR_SHAPE_SHELL:
     case OR_SHAPE_ELLIPSOID: {
       double R2 = 1.0;
       if (s->type == OR_SHAPE_ELLIPSOID) {
@@ -511,7 +524,14 @@ static double shape_cross(const or_shape *s, int D, const double x[3], const int
       double disc = B * B - A * Cc;
       if (disc < 0.0) return -1.0;
       double sq = sqrt(disc), t;
-      if (s->type != OR_SHAPE_SPHERE_OUT) {
+      if (s->type == OR_SHAPE_SHELL) {
+        /* both roots, B -/+ sq over A, in the cancellation-free form; the smaller
+         * one in (0,1] */
+        double qq = B >= 0.0 ? B + sq : B - sq;
+        double ta = qq != 0.0 ? Cc / qq : -1.0, tb = qq / A;
+        double lo = ta < tb ? ta : tb, hi = ta < tb ? tb : ta;
+        t = (lo > 0.0 && lo <= 1.0) ? lo : hi;
+      } else if (s->type != OR_SHAPE_SPHERE_OUT) {
         if (Cc <= 0.0 || B <= 0.0) return -1.0; /* start inside, or moving away */
         t = Cc / (B + sq);                       /* entry root (B - sq)/A */
       } else {
@@ -536,13 +556,14 @@ static double shape_cross(const or_shape *s, int D, const double x[3], const int
 
 long or_geometry(const or_params *p, const uint8_t *base, const double *base_u,
                  const or_shape *shapes, int nshapes, uint8_t *flags, double *q, double *uw,
-                 double *uw1, int32_t *tag) {
+                 double *uw1, int32_t *tag, uint8_t *shell) {
   lat_t L;
   if (lat_load(p->lattice, &L)) return -1;
   const int Q = L.Q, D = L.D;
   const int nx = p->nx, ny = p->ny, nz = p->nz;
   const long N = (long)nx * ny * nz;
-#pragma omp parallel for schedule(static)
+  int on_shell = 0;
+#pragma omp parallel for schedule(static) reduction(| : on_shell)
   for (long n = 0; n < N; ++n) {
     int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long)nx * ny));
     double X[3] = {(double)x, (double)y, (double)z};
@@ -550,8 +571,16 @@ long or_geometry(const or_params *p, const uint8_t *base, const double *base_u,
     if (fl == OR_FLUID)
       for (int k = 0; k < nshapes; ++k)
         if (shape_solid(&shapes[k], D, X)) { fl = OR_SOLID; break; }
+    if (fl == OR_FLUID)
+      for (int k = 0; k < nshapes; ++k) {
+        if (shapes[k].type != OR_SHAPE_SHELL) continue;
+        double d0 = X[0] - shapes[k].c[0], d1 = X[1] - shapes[k].c[1],
+               d2 = D == 3 ? X[2] - shapes[k].c[2] : 0.0;
+        if (d0 * d0 + d1 * d1 + d2 * d2 == shapes[k].r[0] * shapes[k].r[0]) on_shell = 1;
+      }
     flags[n] = fl;
   }
+  if (on_shell) return -2;
   long ncut = 0;
 #pragma omp parallel for schedule(static) reduction(+ : ncut)
   for (long n = 0; n < N; ++n) {
@@ -560,12 +589,21 @@ long or_geometry(const or_params *p, const uint8_t *base, const double *base_u,
     for (int i = 0; i < Q; ++i) {
       long li = n * Q + i;
       double qq = 0.0, u0[3] = {0.0, 0.0, 0.0}, u1[3] = {0.0, 0.0, 0.0};
-      int tg = 0;
+      int tg = 0, sh = 0;
       if (flags[n] == OR_FLUID && i > 0) {
         long m = nbr(p, x, y, z, -L.c[i][0], -L.c[i][1], -L.c[i][2]);
-        if (flags[m] != OR_FLUID) {
+        double Y[3];
+        for (int a = 0; a < 3; ++a) Y[a] = X[a] - L.c[i][a];
+        /* a thin shell between two fluid nodes: 1 seen from outside, 2 from inside */
+        if (flags[m] == OR_FLUID)
+          for (int k = 0; k < nshapes && !sh; ++k)
+            if (shapes[k].type == OR_SHAPE_SHELL) {
+              const int in_x = shell_inside(&shapes[k], D, X), in_y = shell_inside(&shapes[k], D, Y);
+              if (in_x != in_y) sh = in_x ? 2 : 1;
+            }
+        if (flags[m] != OR_FLUID || sh) {
           ++ncut;
-          if (!base || base[m] == OR_FLUID) {
+          if (sh || !base || base[m] == OR_FLUID) {
             /* cut by a shape: nearest crossing along x_F - t c_i */
             double best = 2.0;
             int kb = -1;
@@ -574,11 +612,11 @@ long or_geometry(const or_params *p, const uint8_t *base, const double *base_u,
               if (t > 0.0 && t < best) { best = t; kb = k; }
             }
             if (kb < 0) {
-              best = 1.0; /* rounding left no root: the wall sits on the solid node */
+              best = 1.0; /* rounding left no root: the wall sits on the far node */
               for (int k = 0; k < nshapes; ++k) {
-                double Y[3];
-                for (int a = 0; a < 3; ++a) Y[a] = X[a] - L.c[i][a];
-                if (shape_solid(&shapes[k], D, Y)) { kb = k; break; }
+                const int shell_k = shapes[k].type == OR_SHAPE_SHELL &&
+                                    shell_inside(&shapes[k], D, X) != shell_inside(&shapes[k], D, Y);
+                if (shape_solid(&shapes[k], D, Y) || shell_k) { kb = k; break; }
               }
             }
             qq = best;
@@ -594,7 +632,7 @@ long or_geometry(const or_params *p, const uint8_t *base, const double *base_u,
               u1[1] = s->v1[1] + s->om1[2] * r[0] - s->om1[0] * r[2];
               u1[2] = s->v1[2] + s->om1[0] * r[1] - s->om1[1] * r[0];
               if (D == 2) { u0[2] = 0.0; u1[2] = 0.0; }
-              tg = s->tag;
+              tg = sh == 2 ? -1 : s->tag;
             }
           } else {
             qq = 0.5; /* base-flag wall: half-way */
@@ -607,6 +645,7 @@ long or_geometry(const or_params *p, const uint8_t *base, const double *base_u,
       if (uw) for (int a = 0; a < 3; ++a) uw[li * 3 + a] = u0[a];
       if (uw1) for (int a = 0; a < 3; ++a) uw1[li * 3 + a] = u1[a];
       if (tag) tag[li] = tg;
+      if (shell) shell[li] = (uint8_t)sh;
     }
   }
   return ncut;

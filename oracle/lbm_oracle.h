@@ -40,8 +40,10 @@ enum { OR_NEQ_BOUNCE_BACK = 0, OR_NEQ_REGULARIZED = 1 };
 enum { OR_SHAPE_SPHERE = 0,      /* solid inside |x-c| <= r0 (circle in 2D)        */
        OR_SHAPE_SPHERE_OUT = 1,  /* solid outside |x-c| >= r0                      */
        OR_SHAPE_ELLIPSOID = 2,   /* solid inside sum((x-c)_d/r_d)^2 <= 1 (axis-aligned) */
-       OR_SHAPE_STRIP = 3 };     /* fluid strip |nrm.x - off| < width/2, periodic along nrm
+       OR_SHAPE_STRIP = 3,       /* fluid strip |nrm.x - off| < width/2, periodic along nrm
                                     with period 'period' (0 = not periodic); solid elsewhere */
+       OR_SHAPE_SHELL = 4 };     /* thin spherical shell |x-c| = r0 (a circle in 2D) with fluid
+                                    on both sides (the thin-shell cylinders of Sec. III.B) */
 
 typedef struct {
   int lattice;        /* OR_D2Q9 or OR_D3Q19 */
@@ -86,12 +88,16 @@ void or_init_eq(const or_params *p, const uint8_t *flags, const double *rho,
 /* One collide-stream-boundary update t -> t+1 (push form, two arrays).
  *   flags, q, uw, uw1 describe the geometry at time t; uw1 is the wall velocity
  *   at t+1 (NULL: same as uw; uw NULL: walls at rest).
+ *   shell (N*Q or NULL): nonzero where link i of node n crosses a thin shell to
+ *   the fluid node n - c_i: 1 when n lies outside the shell, 2 inside. Such a
+ *   link is a wall link from both sides: neither node streams across it, and
+ *   each writes its boundary value for the population coming back to it.
  *   f: pre-collision populations at t; fout: pre-collision populations at t+1.
  *   flink (N*Q*3 or NULL): momentum-exchange force of every wall link.
  * Returns 0, or -1 on bad arguments. */
 int or_step(const or_params *p, const uint8_t *flags, const double *q,
-            const double *uw, const double *uw1, const double *f, double *fout,
-            double *flink);
+            const uint8_t *shell, const double *uw, const double *uw1, const double *f,
+            double *fout, double *flink);
 
 /* rho[n], u[n*3 + d] (Guo-corrected velocity) at fluid nodes, 0 elsewhere. */
 void or_macros(const or_params *p, const uint8_t *flags, const double *f,
@@ -109,11 +115,17 @@ void or_refill(const or_params *p, const uint8_t *flags_old, const uint8_t *flag
  *   becomes solid. Links cut by a base-flag node get q = 1/2 and the wall
  *   velocity base_u[m*3..] of that node m (NULL: at rest), tag 0. Links cut by a
  *   shape get the exact q and u_w = v + om x (x_W - c) of the nearest crossing.
- *   Outputs: flags[N], q[N*Q], uw[N*Q*3], uw1[N*Q*3], tag[N*Q] (any output but
- *   flags may be NULL). Returns the number of cut links. */
+ *   A link between two fluid nodes on different sides of a thin shell (one
+ *   inside, |x-c| < r0, one not) is cut from both sides; the inner side's
+ *   links carry tag -1 (their momentum exchange is not counted as a force on
+ *   the shell).
+ *   Outputs: flags[N], q[N*Q], uw[N*Q*3], uw1[N*Q*3], tag[N*Q], shell[N*Q] (the
+ *   marks or_step takes; any output but flags may be NULL). Returns the number
+ *   of cut links, or -2 when a fluid node lies exactly on a thin shell (its
+ *   links would have q = 0 on one side). */
 long or_geometry(const or_params *p, const uint8_t *base, const double *base_u,
                  const or_shape *shapes, int nshapes, uint8_t *flags, double *q,
-                 double *uw, double *uw1, int32_t *tag);
+                 double *uw, double *uw1, int32_t *tag, uint8_t *shell);
 
 /* Interpolation weights the boundary rule applies to its points, for tests:
  * writes up to 3 (s, a) pairs for the scheme at this q and returns their count. */
