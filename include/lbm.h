@@ -82,13 +82,16 @@ enum lbm_status {
 };
 
 /* Analytic shapes for lbm_build_geometry. A node is solid where the shape's test
- * holds (ties count as solid). */
+ * holds (ties count as solid). A thin shell makes no node solid (see
+ * lbm_build_geometry). */
 enum lbm_shape_type {
   LBM_SHAPE_SPHERE = 0,     /* solid inside |x - c| <= r[0] (a circle on D2Q9)            */
   LBM_SHAPE_SPHERE_OUT = 1, /* solid outside |x - c| >= r[0]                               */
   LBM_SHAPE_ELLIPSOID = 2,  /* solid inside sum_d ((x - c)_d / r[d])^2 <= 1, axis-aligned  */
-  LBM_SHAPE_STRIP = 3       /* fluid where |v| < width/2, with v = nrm.x - off. When
+  LBM_SHAPE_STRIP = 3,      /* fluid where |v| < width/2, with v = nrm.x - off. When
                                period > 0, v is first wrapped into [-period/2, period/2) */
+  LBM_SHAPE_SHELL = 4       /* thin spherical shell |x - c| = r[0] >= 1 (a circle on D2Q9)
+                               with fluid on both sides (Sec. III.B-III.C thin shells) */
 };
 
 typedef struct {
@@ -161,7 +164,19 @@ int lbm_set_geometry(lbm_handle h, const uint8_t *flags, const double *q, const 
  * A wall link cut by a base node gets q = 1/2 and that node's velocity, tag 0.
  * A link cut by a shape gets the exact crossing q, the smallest t in (0,1] at
  * which x_F - t c_i reaches the shape, and the rigid-motion velocity
- * v + om x (x_W - c) at the wall point x_W = x_F - q c_i. At most 65536 shapes. */
+ * v + om x (x_W - c) at the wall point x_W = x_F - q c_i. At most 65536 shapes.
+ * Thin shells: a link between two fluid nodes, one strictly inside the shell
+ * (|x - c| < r[0]) and one not, is a wall link of both nodes, each with its own
+ * q (the two add up to 1). Neither node streams across it: each applies the
+ * boundary rule to the population coming back to it, and writes that value into
+ * the slot the other node would have stored. The links on the inner side carry
+ * no force (lbm_wall_force counts the outer fluid only, as for the filled body
+ * of Sec. III.C) and read back with tag -1 from lbm_get_geometry. A shell must
+ * keep at least one node away from the lattice's edges and from other shapes
+ * (two crossings within one link are not represented). LBM_ERR_ARG when a fluid
+ * node lies exactly on a shell (its links would have q = 0 on one side).
+ * lbm_set_geometry cannot express thin shells, and a geometry with thin shells
+ * takes no moving body. */
 int lbm_build_geometry(lbm_handle h, const uint8_t *base, const double *base_u,
                        const lbm_shape *shapes, int nshapes);
 
@@ -204,7 +219,10 @@ int lbm_macros(lbm_handle h, double *rho, double *u);
  * population f*_ibar as in Wen et al.) of the last step. It sums
  * (c_ibar - u_w) f*_ibar(x_F, t) - (c_i - u_w) f_i(x_F, t+1) over the wall links
  * with this tag (tag = -1 sums every tag). Accumulated in FP64 in a fixed
- * order, so the result is deterministic. Synchronises the stream. */
+ * order, so the result is deterministic. Synchronises the stream. On the outer
+ * side of a thin shell f*_ibar(x_F, t) is not kept in memory (the slot holds the
+ * value written from the other side): it is computed again from the state the
+ * last step read, so call this right after a step. */
 int lbm_wall_force(lbm_handle h, int tag, double F[3]);
 
 /* Total mass sum of rho over the fluid nodes, in FP64. Deterministic. Synchronises.
@@ -236,7 +254,8 @@ int lbm_mass(lbm_handle h, double *m);
 int lbm_mass_noalloc(lbm_handle h, double *mass_dev);
 
 /* Read back the geometry the library holds, for checks: flags[N] (lbm_node),
- * q/uw/uw1/tag per link [N*Q(*3)]. Non-wall links read 0. Any pointer may be NULL. */
+ * q/uw/uw1/tag per link [N*Q(*3)]. Non-wall links read 0; links on the inner
+ * side of a thin shell read tag -1. Any pointer may be NULL. */
 int lbm_get_geometry(lbm_handle h, uint8_t *flags, double *q, double *uw, double *uw1,
                      int32_t *tag);
 

@@ -8,6 +8,12 @@
 // solid tests then round exactly like the plain FP64 definition, so the flags
 // are reproducible bit for bit.
 //
+// A thin shell (LBM_SHAPE_SHELL) makes no node solid: a link between two fluid
+// nodes on different sides of it (one strictly inside |x - c| < r0, one not) is
+// a wall link of both nodes, with q measured from each end. The records mark
+// those links (Rec::shell) and the nodes carry F_SHELL; the inner side's links
+// get the force tag TAG_INNER.
+//
 // Candidate shapes of a node come from a uniform cell list. Each cell lists, in
 // increasing shape index, every shape whose bounding box padded by 2 lattice
 // units overlaps the cell. Unbounded shapes (sphere-outside, strip) sit in every
@@ -44,6 +50,7 @@ struct GeoView {
   const int *cell_start;   // [ncell + 1]
   const int *cell_items;
   int cs, cnx, cny, cnz;   // cell size and counts
+  uint32_t *err;           // set to 1 when a fluid node lies exactly on a thin shell
 };
 
 __device__ __forceinline__ int cell_of(const GeoView &g, int x, int y, int z) {
@@ -70,8 +77,14 @@ __device__ bool shape_solid(const GeoShape &s, int D, double x0, double x1, doub
   return false;
 }
 
-// smallest t in (0,1] with x - t e on the shape boundary, entering the solid; -1 if none.
-// Quadratic roots in the cancellation-free form.
+// strictly inside a thin shell
+__device__ __forceinline__ bool shell_inside(const GeoShape &s, int D, double x0, double x1, double x2) {
+  const double d0 = x0 - s.c[0], d1 = x1 - s.c[1], d2 = D == 3 ? x2 - s.c[2] : 0.0;
+  return d0 * d0 + d1 * d1 + d2 * d2 < s.r[0] * s.r[0];
+}
+
+// smallest t in (0,1] with x - t e on the shape boundary, entering the solid (any
+// crossing for a thin shell); -1 if none. Quadratic roots in the cancellation-free form.
 __device__ double shape_cross(const GeoShape &s, int D, const double x[3], const int ci[3]) {
   double d[3], e[3];
   for (int a = 0; a < 3; ++a) {
@@ -102,7 +115,13 @@ __device__ double shape_cross(const GeoShape &s, int D, const double x[3], const
   if (disc < 0.0) return -1.0;
   const double sq = sqrt(disc);
   double t;
-  if (s.type != LBM_SHAPE_SPHERE_OUT) {
+  if (s.type == LBM_SHAPE_SHELL) {
+    // both roots (B -/+ sq) / A; the smaller one when it lies in (0,1]
+    const double qq = B >= 0.0 ? B + sq : B - sq;
+    const double ta = qq != 0.0 ? C / qq : -1.0, tb = qq / A;
+    const double lo = fmin(ta, tb), hi = fmax(ta, tb);
+    t = (lo > 0.0 && lo <= 1.0) ? lo : hi;
+  } else if (s.type != LBM_SHAPE_SPHERE_OUT) {
     if (C <= 0.0 || B <= 0.0) return -1.0;
     t = C / (B + sq);
   } else {
@@ -114,6 +133,30 @@ __device__ double shape_cross(const GeoShape &s, int D, const double x[3], const
 
 template <class L>
 __device__ __forceinline__ void dir(int i, int c[3]) { c[0] = L::cx(i); c[1] = L::cy(i); c[2] = L::cz(i); }
+
+// Links of the fluid node n = (x, y, z) that cross a thin shell to a fluid node
+// (bit i: towards n - c_i). flags: kinds in the low two bits.
+template <class L>
+__device__ uint32_t shell_links(const GeoView &g, const uint8_t *flags, long long n, const Nbr &nb,
+                                int x, int y, int z) {
+  const int cell = cell_of(g, x, y, z);
+  uint32_t m = 0;
+  for (int j = g.cell_start[cell]; j < g.cell_start[cell + 1]; ++j) {
+    const GeoShape &s = g.shapes[g.cell_items[j]];
+    if (s.type != LBM_SHAPE_SHELL) continue;
+    const bool in = shell_inside(s, g.D, (double)x, (double)y, (double)z);
+#pragma unroll 1
+    for (int i = 0; i < L::Q; ++i) {
+      int c[3];
+      dir<L>(i, c);
+      if (c[0] == 0 && c[1] == 0 && c[2] == 0) continue;
+      if ((flags[n + nb.at(-c[0], -c[1], -c[2])] & 3) != K_FLUID) continue;
+      if (shell_inside(s, g.D, (double)(x - c[0]), (double)(y - c[1]), (double)(z - c[2])) != in)
+        m |= 1u << i;
+    }
+  }
+  return m;
+}
 
 // 1. node kinds: the caller's base flags, turned SOLID inside any shape
 __global__ void k_geo_flags(const GeoView g, uint8_t *__restrict__ flags) {
@@ -128,6 +171,13 @@ __global__ void k_geo_flags(const GeoView g, uint8_t *__restrict__ flags) {
     const int cell = cell_of(g, x, y, z);
     for (int j = g.cell_start[cell]; j < g.cell_start[cell + 1]; ++j)
       if (shape_solid(g.shapes[g.cell_items[j]], g.D, (double)x, (double)y, (double)z)) { k = K_SOLID; break; }
+    if (k == K_FLUID)
+      for (int j = g.cell_start[cell]; j < g.cell_start[cell + 1]; ++j) {
+        const GeoShape &s = g.shapes[g.cell_items[j]];
+        if (s.type != LBM_SHAPE_SHELL) continue;
+        const double d0 = x - s.c[0], d1 = y - s.c[1], d2 = g.D == 3 ? z - s.c[2] : 0.0;
+        if (d0 * d0 + d1 * d1 + d2 * d2 == s.r[0] * s.r[0]) *g.err = 1u;
+      }
   }
   flags[n] = k;
 }
@@ -140,7 +190,7 @@ __global__ void k_geo_count(const GeoView g, uint8_t *__restrict__ flags, uint32
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= v.np) return;  // np is a multiple of 32: whole warps leave together
   const int x = (int)(n % v.nxp), y = (int)((n / v.nxp) % v.ny), z = (int)(n / ((long long)v.nxp * v.ny));
-  uint32_t cut = 0, open = 0;
+  uint32_t cut = 0, open = 0, shell = 0;
   const uint8_t k = flags[n] & 3;
   if (k == K_FLUID) {
     Nbr nb;
@@ -152,6 +202,8 @@ __global__ void k_geo_count(const GeoView g, uint8_t *__restrict__ flags, uint32
       if (km == K_SOLID) cut |= 1u << i;
       else if (km == K_OPEN) open |= 1u << i;
     }
+    shell = shell_links<L>(g, flags, n, nb, x, y, z);
+    cut |= shell;
   }
   const bool isb = (cut | open) != 0;
   const uint32_t bal = __ballot_sync(0xffffffffu, isb);
@@ -162,7 +214,7 @@ __global__ void k_geo_count(const GeoView g, uint8_t *__restrict__ flags, uint32
     clink[n >> 5] = nl;
   }
   __syncwarp();
-  if (isb) flags[n] = k | F_BOUNDARY;
+  if (isb) flags[n] = k | F_BOUNDARY | (shell ? F_SHELL : 0);
 }
 
 // 3. exclusive scan of per-chunk counts (three launches: blocks, block totals, add)
@@ -222,16 +274,19 @@ __global__ void k_geo_fill(const GeoView g, const uint32_t *__restrict__ cbase,
   const uint32_t bal = __ballot_sync(0xffffffffu, isb);
   Nbr nb;
   nb.init(v, x, y, z);
-  Rec r = {0u, 0u, 0u, 0u};
+  Rec r = {0u, 0u, 0u, 0u, 0u};
   if (isb) {
+    r.shell = (fl & F_SHELL) ? shell_links<L>(g, v.flags, n, nb, x, y, z) : 0u;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
       if (L::cx(i) == 0 && L::cy(i) == 0 && L::cz(i) == 0) continue;
       const uint8_t km = v.flags[n + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))] & 3;
-      if (km == K_SOLID) r.cut |= 1u << i;
+      if (km == K_SOLID || (r.shell & (1u << i))) r.cut |= 1u << i;
       else if (km == K_OPEN) r.open |= 1u << i;
       else continue;
-      if ((v.flags[n + nb.at(L::cx(i), L::cy(i), L::cz(i))] & 3) == K_FLUID) r.ffok |= 1u << i;
+      // the second node must be fluid and on this node's side of any shell
+      if ((v.flags[n + nb.at(L::cx(i), L::cy(i), L::cz(i))] & 3) == K_FLUID && !((r.shell >> opp<L>(i)) & 1u))
+        r.ffok |= 1u << i;
     }
   }
   // exclusive warp scan of the wall-link counts gives this node's first link
@@ -257,11 +312,12 @@ __global__ void k_geo_fill(const GeoView g, const uint32_t *__restrict__ cbase,
     const long long m = n + nb.at(-c[0], -c[1], -c[2]);
     double qq = 0.5, u0[3] = {0.0, 0.0, 0.0}, u1[3] = {0.0, 0.0, 0.0};
     int tg = 0;
+    const bool across = (r.shell >> i) & 1u;
     // the neighbour's kind in the caller's base flags decides who cut the link
     const int mx = (int)(m % v.nxp), my = (int)((m / v.nxp) % v.ny), mz = (int)(m / ((long long)v.nxp * v.ny));
     const long long hm = ((long long)mz * v.ny + my) * v.nx + mx;
     const uint8_t bk = g.base ? g.base[hm] : (uint8_t)K_FLUID;
-    if (bk != K_FLUID) {
+    if (bk != K_FLUID && !across) {
       if (g.base_u && bk == K_SOLID)
         for (int a = 0; a < 3; ++a) { u0[a] = g.base_u[hm * 3 + a]; u1[a] = u0[a]; }
     } else {
@@ -272,12 +328,21 @@ __global__ void k_geo_fill(const GeoView g, const uint32_t *__restrict__ cbase,
         const double t = shape_cross(g.shapes[k], g.D, X, c);
         if (t > 0.0 && t < best) { best = t; kb = k; }
       }
+      // the first shell (in shape order) whose sides the link joins
+      int ks = -1;
+      if (across)
+        for (int j = g.cell_start[cell]; j < g.cell_start[cell + 1] && ks < 0; ++j) {
+          const GeoShape &s = g.shapes[g.cell_items[j]];
+          if (s.type == LBM_SHAPE_SHELL &&
+              shell_inside(s, g.D, X[0], X[1], X[2]) != shell_inside(s, g.D, X[0] - c[0], X[1] - c[1], X[2] - c[2]))
+            ks = g.cell_items[j];
+        }
       if (kb < 0) {
-        // no root (rounding at a tangent): the wall sits on the solid node
+        // no root (rounding at a tangent): the wall sits on the far node
         best = 1.0;
         for (int j = g.cell_start[cell]; j < g.cell_start[cell + 1]; ++j) {
           const int k = g.cell_items[j];
-          if (shape_solid(g.shapes[k], g.D, X[0] - c[0], X[1] - c[1], X[2] - c[2])) { kb = k; break; }
+          if (shape_solid(g.shapes[k], g.D, X[0] - c[0], X[1] - c[1], X[2] - c[2]) || k == ks) { kb = k; break; }
         }
       }
       qq = best;
@@ -292,7 +357,8 @@ __global__ void k_geo_fill(const GeoView g, const uint32_t *__restrict__ cbase,
         u1[1] = sh.v1[1] + sh.om1[2] * rr[0] - sh.om1[0] * rr[2];
         u1[2] = sh.v1[2] + sh.om1[0] * rr[1] - sh.om1[1] * rr[0];
         if (g.D == 2) { u0[2] = 0.0; u1[2] = 0.0; }
-        tg = sh.tag;
+        const bool inner = ks >= 0 && shell_inside(g.shapes[ks], g.D, X[0], X[1], X[2]);
+        tg = inner ? TAG_INNER : sh.tag;
       }
     }
     if (u0[0] != 0.0 || u0[1] != 0.0 || u0[2] != 0.0 || u1[0] != 0.0 || u1[1] != 0.0 || u1[2] != 0.0)
@@ -331,7 +397,7 @@ void exclusive_scan(uint32_t *a, long long n, uint32_t *tot, uint32_t *total, cu
   } while (0)
 
 static void shape_box(const lbm_shape &s, int D, double lo[3], double hi[3], bool &bounded) {
-  bounded = s.type == LBM_SHAPE_SPHERE || s.type == LBM_SHAPE_ELLIPSOID;
+  bounded = s.type == LBM_SHAPE_SPHERE || s.type == LBM_SHAPE_ELLIPSOID || s.type == LBM_SHAPE_SHELL;
   for (int a = 0; a < 3; ++a) {
     const double r = s.type == LBM_SHAPE_ELLIPSOID ? s.r[a] : s.r[0];
     lo[a] = (a < D) ? s.c[a] - r - 2.0 : -1e300;
@@ -354,7 +420,9 @@ extern "C" int lbm_build_geometry(lbm_handle h, const uint8_t *base, const doubl
   const int D = h->lattice == LBM_D2Q9 ? 2 : 3;
   for (int k = 0; k < nshapes; ++k) {
     const lbm_shape &s = shapes[k];
-    if (s.type < LBM_SHAPE_SPHERE || s.type > LBM_SHAPE_STRIP) return lbm_fail(h, LBM_ERR_ARG, "unknown shape type");
+    if (s.type < LBM_SHAPE_SPHERE || s.type > LBM_SHAPE_SHELL) return lbm_fail(h, LBM_ERR_ARG, "unknown shape type");
+    if (s.type == LBM_SHAPE_SHELL && !(s.r[0] >= 1.0))
+      return lbm_fail(h, LBM_ERR_ARG, "a thin shell's radius must be at least 1");
     if (s.tag < 0 || s.tag > 7) return lbm_fail(h, LBM_ERR_ARG, "shape tags must be 0..7");
     if (s.type == LBM_SHAPE_ELLIPSOID)
       for (int a = 0; a < D; ++a) if (!(s.r[a] > 0.0)) return lbm_fail(h, LBM_ERR_ARG, "ellipsoid axes must be positive");
@@ -414,7 +482,9 @@ extern "C" int lbm_build_geometry(lbm_handle h, const uint8_t *base, const doubl
   GeoShape *d_shapes = nullptr;
   int *d_cstart = nullptr, *d_items = nullptr;
   uint32_t *crec = nullptr, *clink = nullptr, *tot = nullptr, *totals = nullptr;
-  uint32_t htot[2] = {0u, 0u};
+  uint32_t htot[3] = {0u, 0u, 0u};
+  bool has_shell = false;
+  for (int k = 0; k < nshapes; ++k) has_shell = has_shell || shapes[k].type == LBM_SHAPE_SHELL;
   const long long nchunk = h->np / 32;
   const long long nblk = (nchunk + 1023) / 1024;
   GeoView g;
@@ -443,7 +513,8 @@ extern "C" int lbm_build_geometry(lbm_handle h, const uint8_t *base, const doubl
   GEO_CUDA(cudaMalloc(&crec, (nchunk + 1) * sizeof(uint32_t)));
   GEO_CUDA(cudaMalloc(&clink, (nchunk + 1) * sizeof(uint32_t)));
   GEO_CUDA(cudaMalloc(&tot, (nblk + 1) * sizeof(uint32_t)));
-  GEO_CUDA(cudaMalloc(&totals, 2 * sizeof(uint32_t)));
+  GEO_CUDA(cudaMalloc(&totals, 3 * sizeof(uint32_t)));
+  GEO_CUDA(cudaMemsetAsync(totals, 0, 3 * sizeof(uint32_t), st));
 
   g.v = h->view();
   g.D = D;
@@ -453,6 +524,7 @@ extern "C" int lbm_build_geometry(lbm_handle h, const uint8_t *base, const doubl
   g.cell_start = d_cstart;
   g.cell_items = d_items;
   g.cs = cs; g.cnx = cnx; g.cny = cny; g.cnz = cnz;
+  g.err = totals + 2;
   {
     const unsigned blocks = (unsigned)((h->np + 255) / 256);
     k_geo_flags<<<blocks, 256, 0, st>>>(g, h->flags);
@@ -463,14 +535,19 @@ extern "C" int lbm_build_geometry(lbm_handle h, const uint8_t *base, const doubl
     exclusive_scan(crec, nchunk, tot, totals, st);
     exclusive_scan(clink, nchunk, tot, totals + 1, st);
     GEO_CUDA(cudaGetLastError());
-    GEO_CUDA(cudaMemcpyAsync(htot, totals, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    GEO_CUDA(cudaMemcpyAsync(htot, totals, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     GEO_CUDA(cudaStreamSynchronize(st));
+    if (htot[2]) {
+      rc = lbm_fail(h, LBM_ERR_ARG, "a fluid node lies exactly on a thin shell");
+      goto done;
+    }
     // cbase: records before each chunk, plus the total at the end
     GEO_CUDA(cudaMemcpyAsync(h->cbase, crec, nchunk * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
     GEO_CUDA(cudaMemcpyAsync(h->cbase + nchunk, &totals[0], sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
     h->nb = htot[0];
     h->nl = htot[1];
     h->has_uw = moving ? 1 : 0;
+    h->has_shell = has_shell ? 1 : 0;
     const size_t ls = h->link_size();
     if (h->nb) {
       GEO_CUDA(cudaMalloc(&h->rec, h->nb * sizeof(Rec)));
@@ -631,7 +708,7 @@ __global__ void k_move_fill(const MoveGeo g, int koff, const uint8_t *__restrict
   if (r >= rpad) return;
   const View &v = g.v;
   int x = 0, y = 0, z = 0, n = 0;
-  Rec rc = {0u, 0u, 0u, 0u};
+  Rec rc = {0u, 0u, 0u, 0u, 0u};
   Nbr nb;
   if (r < g.rsize) {
     region_xyz(g, r, x, y, z);
@@ -754,7 +831,7 @@ int lbm_sim::move_after_step(void *fout, int set) {
   lf.grid = dim3((unsigned)mb.nfpart);
   lf.block = dim3(256);
   lf.stream = stream;
-  cudaError_t e = launch_force(lattice, dtype, view(), fout, rs, 0, mb.count[s], -1, mb.fpart, lf);
+  cudaError_t e = launch_force(lattice, dtype, view(), fout, nullptr, rs, 0, mb.count[s], -1, mb.fpart, lf);
   if (e == cudaSuccess) e = move_geometry(this, 1, 1, fout, set);
   if (e == cudaSuccess) {
     k_move_advance<<<1, 1, 0, stream>>>(mb.step);
@@ -781,6 +858,7 @@ void lbm_sim::free_moving_body() {
 extern "C" int lbm_set_moving_body(lbm_handle h, const lbm_shape *body, const double *traj, int ntraj, int t0) {
   if (!h || !body || !traj) return lbm_fail(h, LBM_ERR_ARG, "null argument");
   if (!h->geom_ok) return lbm_fail(h, LBM_ERR_STATE, "build the static geometry first");
+  if (h->has_shell) return lbm_fail(h, LBM_ERR_ARG, "a moving body cannot share a geometry with thin shells");
   if (body->type != LBM_SHAPE_SPHERE && body->type != LBM_SHAPE_ELLIPSOID)
     return lbm_fail(h, LBM_ERR_ARG, "a moving body is a sphere or an ellipsoid");
   if (body->tag < 0 || body->tag > 7) return lbm_fail(h, LBM_ERR_ARG, "tags must be 0..7");

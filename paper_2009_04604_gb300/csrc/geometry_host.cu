@@ -64,7 +64,7 @@ int build_records_host(const lbm_sim &s, const uint8_t *flags, const double *q, 
       if (pass == 0 && (g.flags[n] & 3) == K_FLUID) ++g.nfluid;
       const int x = (int)(n % s.nxp), y = (int)((n / s.nxp) % s.ny), z = (int)(n / ((long long)s.nxp * s.ny));
       const long long hn = ((long long)z * s.ny + y) * s.nx + x;
-      Rec r = {0u, 0u, 0u, 0u};
+      Rec r = {0u, 0u, 0u, 0u, 0u};
       for (int i = 0; i < Q; ++i) {
         if (cx[i] == 0 && cy[i] == 0 && cz[i] == 0) continue;
         const long long m = host_neighbour(s, x, y, z, -cx[i], -cy[i], -cz[i]);
@@ -147,7 +147,7 @@ void unpack_geometry(const lbm_sim &s, const HostGeometry &g, uint8_t *flags, do
     for (int i = 0; i < Q; ++i) {
       if (!(r.cut & (1u << i))) continue;
       if (q) q[hn * Q + i] = dbl ? get_val<double>(g.lq, li) : get_val<float>(g.lq, li);
-      if (tag) tag[hn * Q + i] = g.ltag[li];
+      if (tag) tag[hn * Q + i] = g.ltag[li] == TAG_INNER ? -1 : g.ltag[li];
       for (int a = 0; a < 3; ++a) {
         if (g.has_uw) {
           const double u0 = dbl ? get_val<double>(g.luw, li * 3 + a) : get_val<float>(g.luw, li * 3 + a);

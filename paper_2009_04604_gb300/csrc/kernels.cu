@@ -97,11 +97,13 @@ cudaError_t launch_read(int lattice, int dtype, const View &v, const void *fin, 
   });
 }
 
-cudaError_t launch_force(int lattice, int dtype, const View &v, const void *cur, const RecSet &rs,
-                         long long nrec, const int *nrec_dev, int tag, double *part, const Launch &l) {
+cudaError_t launch_force(int lattice, int dtype, const View &v, const void *cur, const void *prev,
+                         const RecSet &rs, long long nrec, const int *nrec_dev, int tag, double *part,
+                         const Launch &l) {
   return dispatch(lattice, dtype, [&]<class L, typename S, typename M>() {
-    k_force<L, S, M><<<l.grid, l.block, 0, l.stream>>>(v, static_cast<const S *>(cur), rs, nrec, nrec_dev,
-                                                       tag, part);
+    k_force<L, S, M><<<l.grid, l.block, 0, l.stream>>>(v, static_cast<const S *>(cur),
+                                                       static_cast<const S *>(prev), rs, nrec,
+                                                       nrec_dev, tag, part);
     return cudaGetLastError();
   });
 }

@@ -489,6 +489,19 @@ __device__ __forceinline__ void boundary_node(const View &v, const RecSet &rs, c
   if (v.wall_neq) neq_stress<L, M>(f, m, pi);
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) fs[i * stride] = f[i];
+  if (r.shell) {
+    // A node with links across a thin shell is relaxed here, not by its lattice
+    // tile. Its post-collision population i streams to n + c_i. When link ibar
+    // crosses the shell, n + c_i is the fluid node on the other side, whose
+    // boundary rule writes that slot ahead: this node stores nothing there.
+    const Par<M> P(v);
+#pragma unroll 1
+    for (int i = 0; i < L::Q; ++i) {
+      const int ib = opp<L>(i);
+      if ((r.shell >> ib) & 1u) continue;
+      fout[v.soff[i] + n] = to_store<S, M>(post_r<L, M>(v, P, i, fs[i * stride], fs[ib * stride], m));
+    }
+  }
   boundary<L, S, M>(v, rs, r, fs, stride, m, pi, n, x, y, z, fout);
 }
 
@@ -525,7 +538,7 @@ __device__ __forceinline__ void lattice_tile(const View &v, const S *__restrict_
   const uint8_t fl = v.flags[n];
   uint32_t bal = 0;
   if (v.bc == BC_BFL) bal = __ballot_sync(0xffffffffu, fl & F_BOUNDARY);
-  if ((fl & 3) != K_FLUID) return;
+  if ((fl & K_LATTICE_MASK) != K_FLUID) return;  // not fluid, or relaxed by its boundary tile
   const int np = (int)v.np;
   M f[L::Q];
   const bool interior = x > 0 && x < v.nx - 1 && y > 0 && y < v.ny - 1 &&
@@ -593,7 +606,7 @@ __device__ __forceinline__ void lattice_tile_pair(const View &v, const S *__rest
   if (y >= v.ny) return;  // uniform across the warp
   const int n = (z * v.ny + y) * v.nxp + x;
   const uint16_t fl2 = *reinterpret_cast<const uint16_t *>(v.flags + n);
-  const bool fa = (fl2 & 3) == K_FLUID, fb = ((fl2 >> 8) & 3) == K_FLUID;
+  const bool fa = (fl2 & K_LATTICE_MASK) == K_FLUID, fb = ((fl2 >> 8) & K_LATTICE_MASK) == K_FLUID;
   if (!__any_sync(0xffffffffu, fa || fb)) return;  // the whole warp is idle
   // offsets of the 9 (dy, dz) source rows, without the x wrap
   const int plane = v.nxp * v.ny;
@@ -824,7 +837,7 @@ __device__ __forceinline__ void tma_lattice(const View &v, const S *__restrict__
   const uint8_t fl = base[lay.template pops_bytes<L>() + ty * lay.W + tx];
   uint32_t bal = 0;
   if (v.bc == BC_BFL) bal = __ballot_sync(0xffffffffu, fl & F_BOUNDARY);
-  if ((fl & 3) != K_FLUID) return;
+  if ((fl & K_LATTICE_MASK) != K_FLUID) return;
   const S *pops = reinterpret_cast<const S *>(base);
   const bool xedge = x == 0 || x >= v.nx - 1;
   const int np = (int)v.np;
@@ -1066,8 +1079,12 @@ __global__ void __launch_bounds__(256) k_read(const View v, const S *__restrict_
 // that is not null), links of one tag (tag < 0: all). It reads the buffer just
 // written: f*_ibar(x_F, t) from the node's own slot and f_i(x_F, t+1) from the
 // written-ahead slot (BFL-completed). Writes a per-block FP64 partial (3 doubles).
+// Links on the inner side of a thin shell (tag TAG_INNER) carry no force. On its
+// outer side the node's own slot ibar holds the value written ahead from the
+// other side, so f*_ibar(x_F, t) is computed again from the state at t, prev.
 template <class L, typename S, typename M>
-__global__ void __launch_bounds__(256) k_force(const View v, const S *__restrict__ cur, RecSet rs,
+__global__ void __launch_bounds__(256) k_force(const View v, const S *__restrict__ cur,
+                                               const S *__restrict__ prev, RecSet rs,
                                                long long nrec, const int *nrec_dev, int tag,
                                                double *__restrict__ part) {
   const long long rid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1083,15 +1100,26 @@ __global__ void __launch_bounds__(256) k_force(const View v, const S *__restrict
     nb.init(v, x, y, z);
     const M *lq = static_cast<const M *>(rs.lq);
     const M *luw = static_cast<const M *>(rs.luw);
+    M fp[L::Q];
+    Macro<L, M> mp = {};
+    if (r.shell && prev) {
+      gather<L, S, M>(v, prev, n, nb, fp);
+      if (v.bc == BC_BFL) bfl_complete<L, M>(v, r, fp);
+      mp = moments<L, M>(v, fp);
+    }
+    const Par<M> P(v);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
       const uint32_t bit = 1u << i;
       if (!(r.cut & bit)) continue;
       const uint32_t li = r.link0 + __popc(r.cut & (bit - 1u));
-      if (tag >= 0 && rs.ltag[li] != tag) continue;
+      const uint8_t lt = rs.ltag[li];
+      if (lt == TAG_INNER || (tag >= 0 && lt != tag)) continue;
       const int ib = opp<L>(i);
       const double w = weight<L>(i);
-      const double fpost_ib = (double)to_math<S, M>(cur[(long long)ib * v.np + n]) + w * v.rho0;
+      const M fpost_m = (r.shell & bit) ? (prev ? post_r<L, M>(v, P, ib, fp[ib], fp[i], mp) : M(0))
+                                        : to_math<S, M>(cur[(long long)ib * v.np + n]);
+      const double fpost_ib = (double)fpost_m + w * v.rho0;
       double fnew = (double)to_math<S, M>(cur[(long long)i * v.np + n + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))]);
       if (v.bc == BC_BFL && (r.ffok & bit)) {
         const M q = lq[li];

@@ -125,16 +125,23 @@ template <> __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16, flo
 }
 
 // Node flag byte: low two bits are the kind, bit 2 marks a fluid node with at
-// least one wall or open link (a boundary node with a record).
-enum : uint8_t { K_FLUID = 0, K_SOLID = 1, K_OPEN = 2, K_PAD = 3, F_BOUNDARY = 4 };
+// least one wall or open link (a boundary node with a record), bit 3 a fluid node
+// with a link across a thin shell (its boundary tile, not a lattice tile, relaxes
+// and stores it).
+enum : uint8_t { K_FLUID = 0, K_SOLID = 1, K_OPEN = 2, K_PAD = 3, F_BOUNDARY = 4, F_SHELL = 8 };
+// Flag bits a lattice tile tests: it relaxes the node only when they are all zero.
+constexpr uint8_t K_LATTICE_MASK = 3 | F_SHELL;
+// Force tag of the links on the inner side of a thin shell: no force is counted there.
+constexpr uint8_t TAG_INNER = 0xFF;
 
 // Boundary record of one boundary node (records are sorted by node index).
 constexpr uint32_t REC_MOVING = 1u << 31;  // in Rec::open: the node has moving wall links
 struct Rec {
-  uint32_t cut;   // bit i: link i is a wall link (node n - c_i is SOLID)
+  uint32_t cut;   // bit i: link i is a wall link (node n - c_i is SOLID, or across a thin shell)
   uint32_t open;  // bit i: link i is an open link (node n - c_i is OPEN); bit 31: REC_MOVING
-  uint32_t ffok;  // bit i: the second node along the link, n + c_i, is fluid (BFL)
+  uint32_t ffok;  // bit i: the second node along the link, n + c_i, is fluid and on this side (BFL)
   uint32_t link0; // index of the first wall link of this node in the link arrays
+  uint32_t shell; // bit i: link i crosses a thin shell to the fluid node n - c_i (also in cut)
 };
 
 // One set of boundary records and their per-link data (math type).

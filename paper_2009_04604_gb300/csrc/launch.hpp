@@ -36,8 +36,11 @@ cudaError_t launch_read(int lattice, int dtype, const View &v, const void *fin, 
                         double *rho, double *u, double *mass_part, const Launch &l);
 // Momentum-exchange partials over the records rs: nrec of them, or *nrec_dev
 // (device) when nrec_dev is not null; the grid must cover the largest count.
-cudaError_t launch_force(int lattice, int dtype, const View &v, const void *cur, const RecSet &rs,
-                         long long nrec, const int *nrec_dev, int tag, double *part, const Launch &l);
+// cur is the state the last step wrote, prev the state it read (used for the
+// links across thin shells; may be null when rs has none).
+cudaError_t launch_force(int lattice, int dtype, const View &v, const void *cur, const void *prev,
+                         const RecSet &rs, long long nrec, const int *nrec_dev, int tag, double *part,
+                         const Launch &l);
 cudaError_t launch_reduce_final(const double *part, long long nblocks, int ncomp, double *out,
                                 cudaStream_t s);
 

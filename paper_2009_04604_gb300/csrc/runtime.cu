@@ -426,8 +426,8 @@ extern "C" int lbm_wall_force(lbm_handle h, int tag, double F[3]) {
   const View v = h->view();
   if (nblk1) {
     l.grid = dim3((unsigned)nblk1);
-    LBM_CUDA(h, launch_force(h->lattice, h->dtype, v, h->f[h->cur], v.stat(), h->nb, nullptr, tag,
-                             h->scratch, l));
+    LBM_CUDA(h, launch_force(h->lattice, h->dtype, v, h->f[h->cur], h->f[h->cur ^ 1], v.stat(), h->nb,
+                             nullptr, tag, h->scratch, l));
   }
   if (nblk2) {
     // the moving body's partials, taken during the last step before its refill
@@ -531,6 +531,7 @@ int lbm_sim::upload(const HostGeometry &g) {
   nl = (long long)g.ltag.size();
   nfluid = g.nfluid;
   has_uw = g.has_uw;
+  has_shell = 0;
   if (nb > 0) {
     LBM_CUDA(this, cudaMalloc(&rec, nb * sizeof(Rec)));
     LBM_CUDA(this, cudaMalloc(&rnode, nb * sizeof(uint32_t)));

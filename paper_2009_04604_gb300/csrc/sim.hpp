@@ -63,6 +63,7 @@ struct lbm_sim {
   uint8_t *ltag = nullptr;
   long long nb = 0, nl = 0, nfluid = 0;
   int has_uw = 0;
+  int has_shell = 0;  // the static geometry has links across thin shells
 
   double *dres = nullptr;     // reduction results (device)
   int *err_dev = nullptr;     // device error word (bit 0: a bounded wait ran out)

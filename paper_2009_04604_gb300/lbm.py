@@ -24,7 +24,7 @@ BC_ELIBB_F, BC_ELIBB_FQ, BC_BFL, BC_HWBB, BC_ELIBB_U, BC_ELIBB_UQ = 0, 1, 2, 3, 
 COLL_BGK, COLL_TRT = 0, 1
 NEQ_BOUNCE_BACK, NEQ_REGULARIZED = 0, 1
 FLUID, SOLID, OPEN = 0, 1, 2
-SHAPE_TYPES = {"sphere": 0, "sphere_out": 1, "ellipsoid": 2, "strip": 3}
+SHAPE_TYPES = {"sphere": 0, "sphere_out": 1, "ellipsoid": 2, "strip": 3, "shell": 4}
 DTYPES = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
 BCS = {"elibb_f": BC_ELIBB_F, "elibb_fq": BC_ELIBB_FQ, "bfl": BC_BFL, "hwbb": BC_HWBB,
        "elibb_u": BC_ELIBB_U, "elibb_uq": BC_ELIBB_UQ}
