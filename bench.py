@@ -159,10 +159,13 @@ def max_over_ranks(dist, x):
     return float(t.item())
 
 
+REC_BYTES = 20  # one boundary record: five 32-bit masks and indices
+
+
 def algorithmic_bytes(nfluid, np_, nb, nl, Q, s, ls, moving):
     """Bytes a launch must move: each fluid population read and written once,
-    one flag byte per (padded) node, 16 B per boundary record, q (and u_w) per wall link."""
-    return nfluid * 2 * Q * s + np_ + nb * 16 + nl * ls * (7 if moving else 1)
+    one flag byte per (padded) node, one record per boundary node, q (and u_w) per wall link."""
+    return nfluid * 2 * Q * s + np_ + nb * REC_BYTES + nl * ls * (7 if moving else 1)
 
 
 # ---------------------------------------------------------------- the oracle CPU baseline
