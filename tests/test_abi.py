@@ -81,3 +81,24 @@ def test_oracle_and_library_share_no_code():
             text = open(os.path.join(root, "oracle", f)).read()
             assert not re.search(r"^\s*(import|from) paper_2009_04604_gb300", text, re.M), f
             assert "include/lbm.h" not in text and "liblbm.so" not in text, f
+
+
+def test_binding_constants_match_the_header():
+    """Every enumerator of include/lbm.h has the same value in the Python binding."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    text = open(os.path.join(root, "include", "lbm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    header = {}
+    for body in re.findall(r"enum\s+\w+\s*\{(.*?)\}", text, flags=re.S):
+        for name, val in re.findall(r"(LBM_\w+)\s*=\s*(-?\d+)", body):
+            header[name] = int(val)
+    assert len(header) >= 30
+    status = {v: k for k, v in lbm.STATUS.items()}
+    shapes = {"LBM_SHAPE_" + k.upper(): v for k, v in lbm.SHAPE_TYPES.items()}
+    for name, val in header.items():
+        if name in status:
+            assert status[name] == val, name
+        elif name.startswith("LBM_SHAPE_"):
+            assert shapes[name] == val, name
+        else:
+            assert getattr(lbm, name[len("LBM_"):]) == val, name
