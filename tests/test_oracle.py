@@ -262,12 +262,13 @@ def _impulsive(bc, q, H, tau=0.8, U=1e-3, tstar=0.05):
     return A.rrse(u[1:H + 1, 0], uth)
 
 
+@pytest.mark.parametrize("q", [0.05, 0.3, 0.75, 1.0])
 @pytest.mark.parametrize("bc", [oracle.BC_ELIBB_F, oracle.BC_ELIBB_FQ, oracle.BC_BFL,
                                 oracle.BC_ELIBB_U, oracle.BC_ELIBB_UQ])
-def test_impulsive_couette_second_order(oracle_lib, bc):
+def test_impulsive_couette_second_order(oracle_lib, bc, q):
     """Impulsively started Couette vs the 100-term series (Eq. solution-couette):
-    second-order convergence of rRSE (Sec. III.A)."""
-    e = [_impulsive(bc, 0.3, H) for H in (10, 20, 40)]
+    second-order convergence of rRSE at every wall position q (Sec. III.A sweeps q)."""
+    e = [_impulsive(bc, q, H) for H in (10, 20, 40)]
     orders = np.log2(np.array(e[:-1]) / np.array(e[1:]))
     assert (orders > 1.8).all(), (e, orders)
     assert e[-1] < 2e-3
