@@ -151,12 +151,20 @@ def barrier(dist):
 
 
 def max_over_ranks(dist, x):
+    """The largest x over all ranks (the slowest rank's time)."""
     if dist is None:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_mlups(world, nfluid, steps, ms):
+    """Whole-job throughput of independent replicas: every rank updates nfluid
+    nodes per step, and the job takes as long as its slowest rank (ms)."""
+    return world * nfluid * steps / (ms * 1e-3) / 1e6
 
 
 REC_BYTES = 20  # one boundary record: five 32-bit masks and indices
@@ -358,7 +366,7 @@ def ours_arm(args, rank, world, dist):
     ms = ev0.elapsed_time(ev1)
     ms = max_over_ranks(dist, ms)
     ms_step = ms / args.steps
-    mlups = world * nfluid * args.steps / (ms * 1e-3) / 1e6
+    mlups = job_mlups(world, nfluid, args.steps, ms)
     # ---- roofline of the step kernel
     peak, peak_kind = measured_peak()
     s_bytes = DTYPE_BYTES[args.dtype]
