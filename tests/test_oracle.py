@@ -479,3 +479,29 @@ def test_wall_velocity_is_rigid_motion(oracle_lib):
         np.testing.assert_allclose(uw[n, i], V + np.cross(Om, xw - cen), atol=1e-16)
         np.testing.assert_allclose(uw1[n, i], 2 * V + np.cross(Om, xw - cen), atol=1e-16)
         assert tag[n, i] == 3
+
+
+@pytest.mark.parametrize("lat", [oracle.D2Q9, oracle.D3Q19, oracle.D3Q27])
+def test_refill_sets_equilibrium_of_rho0_and_body_velocity(oracle_lib, lat):
+    """A node that turns fluid gets f^eq(rho0, u_body): its moments are exactly rho0
+    and rho0 u_body; every other node is left as it was."""
+    c, w, _ = oracle.lattice(lat)
+    dims = (6, 5, 1 if lat == oracle.D2Q9 else 4)
+    p = oracle.params(lat, dims, 0.8, rho0=1.3)
+    N = int(np.prod(dims))
+    rng = np.random.default_rng(2)
+    old = (rng.random(N) < 0.4).astype(np.uint8)         # solid where 1
+    new = np.where(rng.random(N) < 0.5, 0, old).astype(np.uint8)
+    un = 0.05 * rng.standard_normal((N, 3))
+    if lat == oracle.D2Q9:
+        un[:, 2] = 0.0
+    f = rng.random((N, len(w)))
+    f0 = f.copy()
+    oracle.refill(p, old, new, un, f)
+    fresh = (old != oracle.FLUID) & (new == oracle.FLUID)
+    assert fresh.sum() > 3
+    assert np.array_equal(f[~fresh], f0[~fresh])
+    rho = f[fresh].sum(1)
+    j = f[fresh] @ c
+    np.testing.assert_allclose(rho, 1.3, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(j, 1.3 * un[fresh], rtol=0, atol=1e-14)
