@@ -214,7 +214,9 @@ class Simulation:
                                            _np_ptr(tag, ctypes.c_int32)))
 
     def build_geometry(self, base=None, base_u=None, shapes=()):
-        """Link geometry computed on the device from analytic shapes (dict specs)."""
+        """Link geometry computed on the device from analytic shapes: dict specs with the
+        fields of lbm_shape, type one of "sphere", "sphere_out", "ellipsoid", "strip" or
+        "shell" (a thin shell with fluid on both sides)."""
         base = None if base is None else np.ascontiguousarray(np.reshape(base, -1), dtype=np.uint8)
         base_u = _f64(base_u, (-1,))
         arr = make_shapes(list(shapes))
