@@ -52,3 +52,25 @@ def rrse(u, u_th):
     u = np.asarray(u, dtype=np.float64)
     u_th = np.asarray(u_th, dtype=np.float64)
     return float(np.sqrt(np.sum((u - u_th) ** 2) / np.sum(u_th ** 2)))
+
+
+def jeffery_rate(theta, gamma_dot, aspect):
+    """Rotation rate of a prolate ellipsoid (or elliptic cylinder) in simple shear,
+    Jeffery's orbit (Sec. III.C): theta_dot = gamma_dot (r^2 cos^2 theta + sin^2 theta)
+    / (r^2 + 1), theta the major axis's angle from the shear gradient direction.
+    r is read as the aspect ratio r_a / r_b; the printed "equivalent radius" has the
+    dimension of a length, which the rate cannot take."""
+    theta = np.asarray(theta, dtype=np.float64)
+    r2 = aspect * aspect
+    return gamma_dot * (r2 * np.cos(theta) ** 2 + np.sin(theta) ** 2) / (r2 + 1.0)
+
+
+def jeffery_angle(t, gamma_dot, aspect, theta0=0.0):
+    """Closed-form integral of jeffery_rate from theta0 = 0 (major axis along the
+    gradient): tan theta = r tan(gamma_dot t r / (r^2 + 1)), continued across the
+    half-turns."""
+    t = np.asarray(t, dtype=np.float64)
+    assert theta0 == 0.0
+    phase = gamma_dot * t * aspect / (aspect * aspect + 1.0)
+    turns = np.floor(phase / np.pi + 0.5)
+    return np.arctan(aspect * np.tan(phase - turns * np.pi)) + turns * np.pi

@@ -505,3 +505,21 @@ def test_refill_sets_equilibrium_of_rho0_and_body_velocity(oracle_lib, lat):
     j = f[fresh] @ c
     np.testing.assert_allclose(rho, 1.3, rtol=0, atol=1e-14)
     np.testing.assert_allclose(j, 1.3 * un[fresh], rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("aspect", [1.0, 2.0, 3.5])
+def test_jeffery_orbit_period_and_angle(aspect):
+    """Jeffery's orbit (Sec. III.C) against the textbook period
+    T = (2 pi / gamma_dot)(r + 1/r), by quadrature of 1/theta_dot, and the closed-form
+    angle against a Runge-Kutta integration of the rate."""
+    from scipy.integrate import quad, solve_ivp
+    g = 0.013
+    T_quad, _ = quad(lambda th: 1.0 / A.jeffery_rate(th, g, aspect), 0.0, 2.0 * np.pi, limit=400)
+    T = 2.0 * np.pi / g * (aspect + 1.0 / aspect)
+    assert abs(T_quad / T - 1.0) < 1e-10
+    ts = np.linspace(0.0, 1.3 * T, 57)
+    sol = solve_ivp(lambda t, y: A.jeffery_rate(y, g, aspect), (0.0, ts[-1]), [0.0], t_eval=ts,
+                    rtol=1e-11, atol=1e-12)
+    np.testing.assert_allclose(A.jeffery_angle(ts, g, aspect), sol.y[0], atol=1e-8)
+    if aspect > 1.0:  # the long axis lingers along the flow: slowest at theta = pi/2
+        assert A.jeffery_rate(np.pi / 2, g, aspect) < A.jeffery_rate(0.0, g, aspect)
