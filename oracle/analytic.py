@@ -74,3 +74,18 @@ def jeffery_angle(t, gamma_dot, aspect, theta0=0.0):
     phase = gamma_dot * t * aspect / (aspect * aspect + 1.0)
     turns = np.floor(phase / np.pi + 0.5)
     return np.arctan(aspect * np.tan(phase - turns * np.pi)) + turns * np.pi
+
+
+def torque_squared_fluctuation(t, T, order=30):
+    """Torque squared fluctuation (App. D, Eq. TSF30): a least-squares polynomial of
+    the given order through the torque series gives a smooth baseline T_ip; the
+    squared deviation (T - T_ip)^2 is fitted again by a polynomial of the same order.
+    Returns (T_ip, TSF, TSF_ip). The fits use the Chebyshev basis on the span of t,
+    which spans the same polynomials as the monomials and stays well conditioned."""
+    t = np.asarray(t, dtype=np.float64)
+    T = np.asarray(T, dtype=np.float64)
+    Cheb = np.polynomial.Chebyshev
+    T_ip = Cheb.fit(t, T, order)(t)
+    tsf = (T - T_ip) ** 2
+    tsf_ip = Cheb.fit(t, tsf, order)(t)
+    return T_ip, tsf, tsf_ip

@@ -523,3 +523,21 @@ def test_jeffery_orbit_period_and_angle(aspect):
     np.testing.assert_allclose(A.jeffery_angle(ts, g, aspect), sol.y[0], atol=1e-8)
     if aspect > 1.0:  # the long axis lingers along the flow: slowest at theta = pi/2
         assert A.jeffery_rate(np.pi / 2, g, aspect) < A.jeffery_rate(0.0, g, aspect)
+
+
+def test_torque_squared_fluctuation():
+    """App. D: a polynomial torque of degree <= 30 has no fluctuation; a smooth torque
+    plus an alternating term of amplitude eps fluctuates by eps^2 everywhere."""
+    t = np.arange(4000, dtype=np.float64)
+    x = 2.0 * t / t[-1] - 1.0
+    poly = np.polynomial.Chebyshev(np.random.default_rng(1).standard_normal(31))(x)
+    T_ip, tsf, _ = A.torque_squared_fluctuation(t, poly)
+    assert np.abs(T_ip - poly).max() < 1e-9 * np.abs(poly).max()
+    assert tsf.max() < 1e-18 * (poly ** 2).max()
+    eps = 1e-3
+    smooth = np.sin(2.0 * np.pi * t / 3000.0) * np.exp(-t / 5000.0)
+    T = smooth + eps * (-1.0) ** t
+    T_ip, tsf, tsf_ip = A.torque_squared_fluctuation(t, T)
+    inner = slice(100, -100)  # away from the ends, where the alternating term leaks into the fit
+    assert np.abs(T_ip - smooth)[inner].max() < 0.05 * eps
+    np.testing.assert_allclose(tsf_ip[inner], eps ** 2, rtol=0.05)
