@@ -188,6 +188,8 @@ def thin_shell_couette(L, bc, collision=oracle.COLL_BGK, tau=0.8, steps_max=200,
         if change < 1e-10:
             break
     flink = s.run(1, want_force=True)
+    # the force counts the outer fluid only (Sec. III.C): nothing on the inner side
+    assert np.abs(flink[shell == 2]).max() == 0.0 and np.abs(flink[shell == 1]).max() > 0.0
     u = s.macros()[1]
     inner, outer = r < R1, r >= R2
 
