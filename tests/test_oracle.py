@@ -274,6 +274,20 @@ def test_impulsive_couette_second_order(oracle_lib, bc, q):
     assert e[-1] < 2e-3
 
 
+@pytest.mark.parametrize("bc", [oracle.BC_ELIBB_F, oracle.BC_ELIBB_FQ, oracle.BC_BFL,
+                                oracle.BC_ELIBB_U, oracle.BC_ELIBB_UQ])
+def test_impulsive_couette_second_order_over_tau(oracle_lib, bc):
+    """Sec. III.A also sweeps tau: second order at tau = 0.55, 1 and 1.5 (diffusive
+    scaling, the same t* at every H), and under BGK the error grows with tau."""
+    e40 = []
+    for tau in (0.55, 1.0, 1.5):
+        e = [_impulsive(bc, 0.3, H, tau=tau) for H in (10, 20, 40)]
+        orders = np.log2(np.array(e[:-1]) / np.array(e[1:]))
+        assert (orders > 1.8).all(), (tau, e, orders)
+        e40.append(e[-1])
+    assert e40[0] < e40[1] < e40[2], e40
+
+
 def test_impulsive_couette_hwbb_first_order(oracle_lib):
     e = [_impulsive(oracle.BC_HWBB, 0.3, H) for H in (10, 20, 40)]
     orders = np.log2(np.array(e[:-1]) / np.array(e[1:]))
