@@ -262,6 +262,35 @@ int lbm_get_geometry(lbm_handle h, uint8_t *flags, double *q, double *uw, double
 /* Counts of the current geometry: fluid nodes, boundary nodes, wall links. */
 int lbm_get_counts(lbm_handle h, int64_t *n_fluid, int64_t *n_boundary, int64_t *n_links);
 
+/* Checkpoint and resume. The paper has no counterpart: these keep a run's state
+ * so that a resumed run continues bit for bit.
+ * lbm_save writes the state into the caller's host buffer buf of *bytes bytes:
+ * a header (lattice, storage type, size, boundary rule, reference density, a
+ * 64-bit hash of the static geometry, the moving body's identity and pose
+ * index) and the raw stored populations of the current time, the values the
+ * last step wrote ahead for the next one included. With buf NULL it only writes
+ * the size needed into *bytes. LBM_ERR_ARG when *bytes is too small;
+ * LBM_ERR_STATE before a state exists. Synchronises.
+ * lbm_load restores such a state into a handle built with the same lattice,
+ * storage type, size, boundary rule, reference density, static geometry and
+ * moving body (checked against the header: LBM_ERR_ARG otherwise). Relaxation
+ * time, body force and collision are not checked; a resumed run is bitwise
+ * identical to an uninterrupted one when they are the same. A moving body
+ * resumes at the saved pose. The wall force of the step before the save is not
+ * part of the state. Synchronises. */
+int lbm_save(lbm_handle h, void *buf, size_t *bytes);
+int lbm_load(lbm_handle h, const void *buf, size_t bytes);
+
+/* Testing aid for failure detection: how many times a first wait of the
+ * TMA-staged step (launch variant 4) polls its mbarrier before it counts as
+ * hung (default 2^24; a negative value restores it; 0 makes every such wait
+ * run out at once). A wait that runs out sets the handle's device error word,
+ * the block waits for its own copies in flight (always with the default limit)
+ * and leaves, and the next lbm_synchronize returns LBM_ERR_TIMEOUT and clears
+ * the word. The state is then incomplete: re-initialise it. The paper has no
+ * counterpart. */
+int lbm_set_wait_limit(lbm_handle h, long long polls);
+
 /* Launch configuration of the step kernel:
  *   bx x by threads per block: bx a multiple of 32 that divides the padded row
  *     length, bx*by <= 256;

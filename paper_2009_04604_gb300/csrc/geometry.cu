@@ -217,6 +217,27 @@ __global__ void k_geo_count(const GeoView g, uint8_t *__restrict__ flags, uint32
   if (isb) flags[n] = k | F_BOUNDARY | (shell ? F_SHELL : 0);
 }
 
+// Planes of a non-fluid node whose slot receives a value written ahead: bit i when
+// the node n + c_i is fluid (its link i is a wall or open link, and the step
+// writes its incoming population into slot (i, n)). Fluid and padding nodes get 0.
+template <class L>
+__global__ void k_geo_amask(const View v, uint32_t *__restrict__ amask) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= v.np) return;
+  const int x = (int)(n % v.nxp), y = (int)((n / v.nxp) % v.ny), z = (int)(n / ((long long)v.nxp * v.ny));
+  uint32_t m = 0;
+  if (x < v.nx && (v.flags[n] & 3) != K_FLUID) {
+    Nbr nb;
+    nb.init(v, x, y, z);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      if (L::cx(i) == 0 && L::cy(i) == 0 && L::cz(i) == 0) continue;
+      if ((v.flags[n + nb.at(L::cx(i), L::cy(i), L::cz(i))] & 3) == K_FLUID) m |= 1u << i;
+    }
+  }
+  amask[n] = m;
+}
+
 // 3. exclusive scan of per-chunk counts (three launches: blocks, block totals, add)
 __global__ void k_scan_block(uint32_t *__restrict__ a, long long n, uint32_t *__restrict__ tot) {
   __shared__ uint32_t ws[32];
@@ -370,6 +391,14 @@ __global__ void k_geo_fill(const GeoView g, const uint32_t *__restrict__ cbase,
   }
   if (moving_node) r.open |= REC_MOVING;
   rec[rid] = r;
+}
+
+cudaError_t launch_amask(int lattice, const View &v, uint32_t *amask, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((v.np + 255) / 256);
+  if (lattice == 0) k_geo_amask<D2Q9><<<blocks, 256, 0, s>>>(v, amask);
+  else if (lattice == 1) k_geo_amask<D3Q19><<<blocks, 256, 0, s>>>(v, amask);
+  else k_geo_amask<D3Q27><<<blocks, 256, 0, s>>>(v, amask);
+  return cudaGetLastError();
 }
 
 }  // namespace lbm
@@ -584,6 +613,8 @@ extern "C" int lbm_build_geometry(lbm_handle h, const uint8_t *base, const doubl
       for (long long n = 0; n < h->np; ++n) nf += (fl[n] & 3) == K_FLUID;
       h->nfluid = nf;
     }
+    rc = h->finish_geometry();
+    if (rc) goto done;
     h->geom_ok = true;
   }
 done:
@@ -663,7 +694,7 @@ __global__ void k_move_update(const MoveGeo g, int koff, int refill, uint8_t *__
       fout[(long long)i * v.np + n + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))] =
           to_store<S, M>(feq_s<L, M>(i, M(0), M(v.rho0), ux, uy, uz, usq));
   }
-  flags[n] = now;
+  flags[n] = now | F_KEEP;  // the lattice tiles never store into the region's non-fluid slots
 }
 
 // per 32-node region chunk: records and wall links (the region's fluid nodes whose
@@ -841,6 +872,15 @@ int lbm_sim::move_after_step(void *fout, int set) {
   return LBM_OK;
 }
 
+int lbm_sim::move_rebuild(long long pose) {
+  const int k = (int)pose;
+  LBM_CUDA_GEO(this, cudaMemcpyAsync(mb.step, &k, sizeof(int), cudaMemcpyHostToDevice, stream));
+  cudaError_t e = move_geometry(this, 0, 0, f[cur], cur);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return lbm_fail(this, LBM_ERR_CUDA, std::string("moving body: ") + cudaGetErrorString(e));
+  return LBM_OK;
+}
+
 void lbm_sim::free_moving_body() {
   if (!mb.on && !mb.traj) return;
   cudaStreamSynchronize(stream);
@@ -934,6 +974,14 @@ extern "C" int lbm_set_moving_body(lbm_handle h, const lbm_shape *body, const do
   LBM_CUDA_GEO(h, cudaMemcpyAsync(mb.shape, &gs, sizeof(GeoShape), cudaMemcpyHostToDevice, h->stream));
   LBM_CUDA_GEO(h, cudaMemcpyAsync(mb.traj, traj, sizeof(double) * 9 * ntraj, cudaMemcpyHostToDevice, h->stream));
   LBM_CUDA_GEO(h, cudaMemcpyAsync(mb.step, &t0, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  {  // identity of the body for lbm_save / lbm_load
+    unsigned long long hh = 0xcbf29ce484222325ULL;
+    const unsigned char *pb = reinterpret_cast<const unsigned char *>(&gs);
+    for (size_t k = 0; k < sizeof(GeoShape); ++k) hh = (hh ^ pb[k]) * 0x100000001b3ULL;
+    const unsigned char *pt = reinterpret_cast<const unsigned char *>(traj);
+    for (size_t k = 0; k < sizeof(double) * 9 * (size_t)ntraj; ++k) hh = (hh ^ pt[k]) * 0x100000001b3ULL;
+    mb.hash = hh;
+  }
   mb.on = true;
   ++h->version;
   h->tiles_bx = h->tiles_by = 0;

@@ -78,6 +78,42 @@ __device__ __forceinline__ const Rec *record_of(const View &v, long long n, uint
   return v.rec + v.cbase[n >> 5] + __popc(bal & lt);
 }
 
+// Whether a non-fluid node's lattice lane stores into its slots: when the 32-byte
+// sector of its slots holds a fluid node, so that the warp writes the sector
+// whole, and unless it lies in a moving body's region. It then stores every
+// plane that takes no written-ahead value (View::amask) and the values are
+// never read. fluid_bal is the warp ballot of the fluid test, one bit per
+// `per` consecutive nodes of each lane (a lane's nodes never straddle a sector).
+template <typename S>
+__device__ __forceinline__ bool fills_sector(uint8_t fl, uint32_t fluid_bal, int per) {
+  constexpr int kNodes = 32 / (int)sizeof(S);  // nodes per 32-byte sector
+  const int lanes = kNodes / per >= 32 ? 32 : kNodes / per;
+  const int lane = threadIdx.x & 31;
+  const uint32_t grp = lanes >= 32 ? 0xffffffffu : (((1u << lanes) - 1u) << (lane & ~(lanes - 1)));
+  return (fl & 3) != K_FLUID && !(fl & F_KEEP) && (fluid_bal & grp) != 0;
+}
+
+// Explicitly rounded operations (Ex<M>: one rounding per multiply, add and fused
+// multiply-add, in the order written). The moments, the relaxation and the
+// boundary rule are written with them: the compiler is then free neither to fuse
+// nor to split an operation, so every kernel that inlines them (the step
+// variants, the batched step, the TMA-staged step) rounds exactly alike.
+template <typename M> struct Ex;
+template <> struct Ex<float> {
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+};
+template <> struct Ex<double> {
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+  static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+};
+
 // ---------------------------------------------------------------- moments, equilibrium
 template <class L, typename M>
 struct Macro {
@@ -86,34 +122,49 @@ struct Macro {
 
 // Density deviation and Guo-corrected velocity, summed over opposite pairs
 // (f_i + f_ibar and f_i - f_ibar), with the rest population in the middle slot.
-template <class L, typename M>
+// U: f in the units of the stored values (Units<S>), with Par's stored-units rho0 and F.
+template <class L, typename M, bool U = false>
 __device__ __forceinline__ Macro<L, M> moments(const View &v, const M (&f)[L::Q]) {
+  using X = Ex<M>;
   constexpr int R = L::Q / 2;
   M d = f[R], jx = M(0), jy = M(0), jz = M(0);
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const int j = L::Q - 1 - i;
-    const M sum = f[i] + f[j], dif = f[i] - f[j];
-    d += sum;
-    if (L::cx(i) > 0) jx += dif; else if (L::cx(i) < 0) jx -= dif;
-    if (L::cy(i) > 0) jy += dif; else if (L::cy(i) < 0) jy -= dif;
-    if (L::cz(i) > 0) jz += dif; else if (L::cz(i) < 0) jz -= dif;
+    const M sum = X::add(f[i], f[j]), dif = X::sub(f[i], f[j]);
+    d = X::add(d, sum);
+    if (L::cx(i) > 0) jx = X::add(jx, dif); else if (L::cx(i) < 0) jx = X::sub(jx, dif);
+    if (L::cy(i) > 0) jy = X::add(jy, dif); else if (L::cy(i) < 0) jy = X::sub(jy, dif);
+    if (L::cz(i) > 0) jz = X::add(jz, dif); else if (L::cz(i) < 0) jz = X::sub(jz, dif);
   }
-  const Par<M> P(v);
+  const Par<M> P(v, U);
   Macro<L, M> m;
   m.drho = d;
-  m.rho = P.rho0 + d;
-  const M inv = M(1) / m.rho;
+  m.rho = X::add(P.rho0, d);
+  const M inv = X::div(M(1), m.rho);
   if (v.has_force) {  // Guo: u = (sum c f + F/2) / rho
-    jx += M(0.5) * P.F[0];
-    jy += M(0.5) * P.F[1];
-    jz += M(0.5) * P.F[2];
+    jx = X::fma(M(0.5), P.F[0], jx);
+    jy = X::fma(M(0.5), P.F[1], jy);
+    jz = X::fma(M(0.5), P.F[2], jz);
   }
-  m.ux = jx * inv;
-  m.uy = jy * inv;
-  m.uz = jz * inv;
-  m.usq = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
+  m.ux = X::mul(jx, inv);
+  m.uy = X::mul(jy, inv);
+  m.uz = X::mul(jz, inv);
+  m.usq = X::fma(m.uz, m.uz, X::fma(m.uy, m.uy, X::mul(m.ux, m.ux)));
   return m;
+}
+
+// c_i . a for a compile-time direction i: a signed sum of the components, each
+// added or subtracted in the order x, y, z (the selection itself is exact)
+template <class L, typename M>
+__device__ __forceinline__ M cdot_c(int i, M ax, M ay, M az) {
+  using X = Ex<M>;
+  M r = M(0);
+  bool any = false;
+  if (L::cx(i) != 0) { r = L::cx(i) > 0 ? ax : -ax; any = true; }
+  if (L::cy(i) != 0) { r = any ? (L::cy(i) > 0 ? X::add(r, ay) : X::sub(r, ay)) : (L::cy(i) > 0 ? ay : -ay); any = true; }
+  if (L::cz(i) != 0) { r = any ? (L::cz(i) > 0 ? X::add(r, az) : X::sub(r, az)) : (L::cz(i) > 0 ? az : -az); }
+  return r;
 }
 
 // shifted equilibrium f^eq_i(rho, u) - w_i rho0 = w_i [drho + rho (3 cu + 9/2 cu^2 - 3/2 u^2)]
@@ -138,89 +189,99 @@ enum : int { PH_FORCE = 1, PH_TRT = 2 };
 //    k+- = 1 - omega+-/2, omega+ = 1/tau and omega- follows from the magic
 //    parameter (Eq. magic-parameter).
 // The relaxed value of direction i goes to put(i, value); collide_store writes it
-// to the output planes, post_all to registers.
-template <class L, typename M, int PHYS, class Put>
+// to the output planes, post_all to registers. Every operation is explicitly
+// rounded (Ex<M>), so that all kernels relax a node bit for bit alike.
+template <class L, typename M, int PHYS, bool U, class Put>
 __device__ __forceinline__ void relax(const View &v, const M (&f)[L::Q], const Macro<L, M> &m, Put &&put) {
+  using X = Ex<M>;
   constexpr bool FORCE = (PHYS & PH_FORCE) != 0, TRT = (PHYS & PH_TRT) != 0;
   constexpr int R = L::Q / 2;
-  const Par<M> P(v);
-  const M om = P.omega, omr = M(1) - om;
-  M Fx = M(0), Fy = M(0), Fz = M(0), kf = M(0), km = M(0), uF = M(0);
+  const Par<M> P(v, U);
+  const M om = P.omega, omr = X::sub(M(1), om);
+  M Fx = M(0), Fy = M(0), Fz = M(0), kf = M(0), km = M(0), uF3 = M(0);
   if constexpr (FORCE) {
     Fx = P.F[0]; Fy = P.F[1]; Fz = P.F[2];
-    kf = M(1) - M(0.5) * om;
-    if constexpr (TRT) km = M(1) - M(0.5) * P.omega_m;
-    uF = m.ux * Fx + m.uy * Fy + m.uz * Fz;
+    kf = X::fma(M(-0.5), om, M(1));
+    if constexpr (TRT) km = X::fma(M(-0.5), P.omega_m, M(1));
+    uF3 = X::mul(M(-3), X::fma(m.uz, Fz, X::fma(m.uy, Fy, X::mul(m.ux, Fx))));  // -3 u.F
   }
   if constexpr (TRT) {
     const M omm = P.omega_m;
-    const M d0 = m.drho - M(1.5) * m.rho * m.usq;
+    const M d0 = X::fma(X::mul(M(-1.5), m.rho), m.usq, m.drho);
+    const M rho45 = X::mul(M(4.5), m.rho);
     {
       const M w = M(weight<L>(R));
-      M r = f[R] + om * (w * d0 - f[R]);
-      if constexpr (FORCE) r -= M(3) * kf * w * uF;
+      M r = X::fma(om, X::sub(X::mul(w, d0), f[R]), f[R]);
+      if constexpr (FORCE) r = X::fma(X::mul(w, kf), uF3, r);
       put(R, r);
     }
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       const int j = L::Q - 1 - i;
-      const M w = M(weight<L>(i));
-      const M cu = M(L::cx(i)) * m.ux + M(L::cy(i)) * m.uy + M(L::cz(i)) * m.uz;
-      const M ep = w * (d0 + M(4.5) * m.rho * cu * cu), em = M(3) * w * m.rho * cu;
-      M dp = om * (ep - M(0.5) * (f[i] + f[j]));
-      M dm = omm * (em - M(0.5) * (f[i] - f[j]));
+      const M w = M(weight<L>(i)), w3 = M(3.0 * weight<L>(i));
+      const M cu = cdot_c<L, M>(i, m.ux, m.uy, m.uz);
+      const M ep = X::mul(w, X::fma(X::mul(rho45, cu), cu, d0)), em = X::mul(X::mul(w3, m.rho), cu);
+      M dp = X::mul(om, X::fma(M(-0.5), X::add(f[i], f[j]), ep));
+      M dm = X::mul(omm, X::fma(M(-0.5), X::sub(f[i], f[j]), em));
       if constexpr (FORCE) {
-        const M cF = M(L::cx(i)) * Fx + M(L::cy(i)) * Fy + M(L::cz(i)) * Fz;
-        dp += kf * w * (M(9) * cu * cF - M(3) * uF);
-        dm += M(3) * km * w * cF;
+        const M cF = cdot_c<L, M>(i, Fx, Fy, Fz);
+        dp = X::fma(X::mul(kf, w), X::fma(X::mul(M(9), cu), cF, uF3), dp);
+        dm = X::fma(X::mul(km, w3), cF, dm);
       }
-      put(i, f[i] + (dp + dm));
-      put(j, f[j] + (dp - dm));
+      put(i, X::add(f[i], X::add(dp, dm)));
+      put(j, X::add(f[j], X::sub(dp, dm)));
     }
   } else {
-    const M wr = om * m.rho;
-    const M b0 = om * (m.drho - M(1.5) * m.rho * m.usq);
+    const M wr = X::mul(om, m.rho);
+    const M b0 = X::mul(om, X::fma(X::mul(M(-1.5), m.rho), m.usq, m.drho));
+    const M wr45 = X::mul(M(4.5), wr);
     {
       const M w = M(weight<L>(R));
-      M eq = w * b0;
-      if constexpr (FORCE) eq -= M(3) * kf * w * uF;
-      put(R, omr * f[R] + eq);
+      M eq = X::mul(w, b0);
+      if constexpr (FORCE) eq = X::fma(X::mul(w, kf), uF3, eq);
+      put(R, X::fma(omr, f[R], eq));
     }
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       const int j = L::Q - 1 - i;
-      const M w = M(weight<L>(i));
-      const M cu = M(L::cx(i)) * m.ux + M(L::cy(i)) * m.uy + M(L::cz(i)) * m.uz;
-      M sym = w * (b0 + M(4.5) * wr * cu * cu);
-      M asym = M(3) * w * wr * cu;
+      const M w = M(weight<L>(i)), w3 = M(3.0 * weight<L>(i));
+      const M cu = cdot_c<L, M>(i, m.ux, m.uy, m.uz);
+      M sym = X::mul(w, X::fma(X::mul(wr45, cu), cu, b0));
+      M asym = X::mul(X::mul(w3, wr), cu);
       if constexpr (FORCE) {
-        const M cF = M(L::cx(i)) * Fx + M(L::cy(i)) * Fy + M(L::cz(i)) * Fz;
-        sym += kf * w * (M(9) * cu * cF - M(3) * uF);
-        asym += M(3) * kf * w * cF;
+        const M cF = cdot_c<L, M>(i, Fx, Fy, Fz);
+        sym = X::fma(X::mul(kf, w), X::fma(X::mul(M(9), cu), cF, uF3), sym);
+        asym = X::fma(X::mul(kf, w3), cF, asym);
       }
-      put(i, omr * f[i] + (sym + asym));
-      put(j, omr * f[j] + (sym - asym));
+      put(i, X::fma(omr, f[i], X::add(sym, asym)));
+      put(j, X::fma(omr, f[j], X::sub(sym, asym)));
     }
   }
 }
 
+// The lattice tiles' relaxation, in the units of the stored values (Units<S>).
+// skip: planes not to store (bit i); 0 for fluid nodes.
 template <class L, typename S, typename M, int PHYS>
 __device__ __forceinline__ void collide_store(const View &v, const M (&f)[L::Q], const Macro<L, M> &m,
-                                              S *__restrict__ dst, int np) {
-  relax<L, M, PHYS>(v, f, m, [&](int i, M val) { dst[i * np] = to_store<S, M>(val); });
+                                              S *__restrict__ dst, int np, uint32_t skip) {
+  relax<L, M, PHYS, Units<S>::kStored>(v, f, m, [&](int i, M val) {
+    if (!((skip >> i) & 1u)) dst[i * np] = Units<S>::template store<M>(val);
+  });
 }
 
 // The same, storing node n's planes at the view's precomputed plane offsets.
 template <class L, typename S, typename M, int PHYS>
 __device__ __forceinline__ void collide_store_at(const View &v, const M (&f)[L::Q], const Macro<L, M> &m,
-                                                 S *__restrict__ fout, int n) {
-  relax<L, M, PHYS>(v, f, m, [&](int i, M val) { fout[v.soff[i] + n] = to_store<S, M>(val); });
+                                                 S *__restrict__ fout, int n, uint32_t skip) {
+  relax<L, M, PHYS, Units<S>::kStored>(v, f, m, [&](int i, M val) {
+    if (!((skip >> i) & 1u)) fout[v.soff[i] + n] = Units<S>::template store<M>(val);
+  });
 }
 
-template <class L, typename M, int PHYS>
+template <class L, typename M, int PHYS, bool U>
 __device__ __forceinline__ void post_all(const View &v, const M (&f)[L::Q], const Macro<L, M> &m,
                                          M (&out)[L::Q]) {
-  relax<L, M, PHYS>(v, f, m, [&](int i, M val) { out[i] = val; });
+  relax<L, M, PHYS, U>(v, f, m, [&](int i, M val) { out[i] = val; });
 }
 
 // ---------------------------------------------------------------- boundary rule
@@ -244,26 +305,6 @@ __device__ __forceinline__ void post_all(const View &v, const M (&f)[L::Q], cons
 // The loop runs over the set bits of the link masks with a run-time direction
 // index, which keeps the code small. The node's populations sit in shared memory
 // (fs[i*stride]), and the direction constants come from packed words.
-
-// The rule is written with explicitly rounded operations (Ex<M>: one rounding
-// per multiply, add and fused multiply-add, in the order written). The compiler
-// is then free neither to fuse nor to split them, so every kernel that inlines
-// the rule (the step variants, the batched step) rounds exactly alike.
-template <typename M> struct Ex;
-template <> struct Ex<float> {
-  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
-  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
-  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
-  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
-};
-template <> struct Ex<double> {
-  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
-  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
-  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
-  static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
-  static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
-};
 
 // c_i . a for a run-time direction
 template <class L, typename M>
@@ -526,7 +567,11 @@ __device__ __forceinline__ void boundary_node(const View &v, const RecSet &rs, c
 // PHYS selects the body-force path and the collision (PH_FORCE, PH_TRT) at
 // compile time. Element offsets are 32-bit,
 // since the library keeps Q x padded nodes below 2^31 per simulation.
-// Lattice tile {z, t} of the table: gather, relax and store every fluid node.
+// Lattice tile {z, t} of the table: gather, relax and store every fluid node (in
+// the units of the stored values, Units<S>). A non-fluid node whose 32-byte sector
+// holds a fluid node stores the relaxation of zeros into the planes that take no
+// written-ahead value, values that nothing reads, so that the warp writes every
+// sector it touches whole.
 template <class L, typename S, typename M, int PHYS>
 __device__ __forceinline__ void lattice_tile(const View &v, const S *__restrict__ fin,
                                              S *__restrict__ fout, int2 tile) {
@@ -536,29 +581,42 @@ __device__ __forceinline__ void lattice_tile(const View &v, const S *__restrict_
   if (y >= v.ny) return;  // uniform across the warp
   const int n = (z * v.ny + y) * v.nxp + x;
   const uint8_t fl = v.flags[n];
+  const uint32_t fbal = __ballot_sync(0xffffffffu, (fl & 3) == K_FLUID);
+  if (!fbal) return;  // the whole warp is idle
   uint32_t bal = 0;
   if (v.bc == BC_BFL) bal = __ballot_sync(0xffffffffu, fl & F_BOUNDARY);
-  if ((fl & K_LATTICE_MASK) != K_FLUID) return;  // not fluid, or relaxed by its boundary tile
+  const bool here = (fl & K_LATTICE_MASK) == K_FLUID;  // fluid, and not relaxed by its boundary tile
+  const bool fill = fills_sector<S>(fl, fbal, 1);      // a non-fluid node completing a sector
+  const bool masked = __any_sync(0xffffffffu, fill);   // the warp's stores need the per-plane masks
+  if (!here && !fill) return;
   const int np = (int)v.np;
   M f[L::Q];
-  const bool interior = x > 0 && x < v.nx - 1 && y > 0 && y < v.ny - 1 &&
-                        (L::D == 2 || (z > 0 && z < v.nz - 1));
-  if (interior) {
-    // no wrap: the source of population i is n - c_i, at an offset that is the same
-    // for every thread and precomputed on the host (loff)
+  uint32_t skip = 0;
+  if (here) {
+    const bool interior = x > 0 && x < v.nx - 1 && y > 0 && y < v.ny - 1 &&
+                          (L::D == 2 || (z > 0 && z < v.nz - 1));
+    if (interior) {
+      // no wrap: the source of population i is n - c_i, at an offset that is the
+      // same for every thread and precomputed on the host (loff)
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) f[i] = to_math<S, M>(__ldg(fin + (v.loff[i] + n)));
+      for (int i = 0; i < L::Q; ++i) f[i] = Units<S>::template load<M>(__ldg(fin + (v.loff[i] + n)));
+    } else {
+      Nbr nb;
+      nb.init(v, x, y, z);
+      const S *__restrict__ src = fin + n;
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i)
+        f[i] = Units<S>::template load<M>(__ldg(src + (i * np + nb.at(-L::cx(i), -L::cy(i), -L::cz(i)))));
+    }
+    if (v.bc == BC_BFL && (fl & F_BOUNDARY)) bfl_complete<L, M>(v, *record_of(v, n, bal), f);
   } else {
-    Nbr nb;
-    nb.init(v, x, y, z);
-    const S *__restrict__ src = fin + n;
+    skip = v.amask[n];
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i)
-      f[i] = to_math<S, M>(__ldg(src + (i * np + nb.at(-L::cx(i), -L::cy(i), -L::cz(i)))));
+    for (int i = 0; i < L::Q; ++i) f[i] = M(0);
   }
-  if (v.bc == BC_BFL && (fl & F_BOUNDARY)) bfl_complete<L, M>(v, *record_of(v, n, bal), f);
-  const Macro<L, M> m = moments<L, M>(v, f);
-  collide_store_at<L, S, M, PHYS>(v, f, m, fout, n);
+  const Macro<L, M> m = moments<L, M, Units<S>::kStored>(v, f);
+  if (masked) collide_store_at<L, S, M, PHYS>(v, f, m, fout, n, skip);
+  else collide_store_at<L, S, M, PHYS>(v, f, m, fout, n, 0u);
 }
 
 // ---------------------------------------------------------------- two nodes per thread
@@ -571,9 +629,11 @@ __device__ __forceinline__ void lattice_tile(const View &v, const S *__restrict_
 // x wrap, with its shear), take one scalar load per such plane instead. All loads
 // are issued before any value is used, since a shuffle waits for its load. Both
 // nodes are then relaxed as in lattice_tile. A pair whose two nodes are fluid is
-// stored with one vector store per plane, otherwise node by node, so that the
-// slots of a non-fluid node (which may hold written-ahead values) are never
-// touched. Not used with BFL, whose record lookup assumes one node per lane.
+// stored with one vector store per plane. A non-fluid node next to a fluid one
+// stores into the planes whose slot takes no written-ahead value (View::amask),
+// so that the sector is written whole; with such a value in the pair, the pair
+// is stored node by node and plane by plane. Not used with BFL, whose record
+// lookup assumes one node per lane.
 template <typename S> struct Vec2;
 template <> struct Vec2<float> {
   using T = float2;
@@ -581,7 +641,7 @@ template <> struct Vec2<float> {
   __device__ static float hi(T v) { return v.y; }
   __device__ static T make(float a, float b) { return make_float2(a, b); }
 };
-template <> struct Vec2<__half> {
+template <> struct Vec2<__half> {  // in the units of the stored values (Units<__half>)
   using T = __half2;
   __device__ static float lo(T v) { return __low2float(v); }
   __device__ static float hi(T v) { return __high2float(v); }
@@ -606,8 +666,14 @@ __device__ __forceinline__ void lattice_tile_pair(const View &v, const S *__rest
   if (y >= v.ny) return;  // uniform across the warp
   const int n = (z * v.ny + y) * v.nxp + x;
   const uint16_t fl2 = *reinterpret_cast<const uint16_t *>(v.flags + n);
-  const bool fa = (fl2 & K_LATTICE_MASK) == K_FLUID, fb = ((fl2 >> 8) & K_LATTICE_MASK) == K_FLUID;
-  if (!__any_sync(0xffffffffu, fa || fb)) return;  // the whole warp is idle
+  const uint8_t fla = (uint8_t)(fl2 & 0xff), flb = (uint8_t)(fl2 >> 8);
+  const bool fa = (fla & K_LATTICE_MASK) == K_FLUID, fb = (flb & K_LATTICE_MASK) == K_FLUID;
+  const uint32_t fbal = __ballot_sync(0xffffffffu, (fla & 3) == K_FLUID || (flb & 3) == K_FLUID);
+  if (!fbal) return;  // the whole warp is idle
+  // stores: the nodes relaxed here, and non-fluid nodes that complete a sector
+  // with a fluid node (every plane that takes no written-ahead value)
+  const bool ga = fills_sector<S>(fla, fbal, 2), gb = fills_sector<S>(flb, fbal, 2);
+  const bool sa = fa || ga, sb = fb || gb;
   // offsets of the 9 (dy, dz) source rows, without the x wrap
   const int plane = v.nxp * v.ny;
   int ro[3][3];
@@ -628,19 +694,34 @@ __device__ __forceinline__ void lattice_tile_pair(const View &v, const S *__rest
   // the element per x-shifted plane that the neighbouring lanes cannot supply:
   // c_ix = +1: x-1 at lane 0 (wrapping when x = 0); c_ix = -1: x+1 when it leaves
   // the row (node x+1 is then padding), else x+2 at lane 31 or when it wraps
+  // Away from the row ends that element sits in the pair's own source row, one
+  // before or two after the pair; only a warp holding a row end takes the
+  // periodic (and sheared) wrap.
   const bool wa = x + 1 >= v.nx;
   const bool need_up = lane == 0, need_dn = wa || lane == 31 || x + 2 >= v.nx;
   M e[L::Q];
+  if (__any_sync(0xffffffffu, x == 0 || x + 2 >= v.nx)) {
 #pragma unroll
-  for (int i = 0; i < L::Q; ++i) {
-    const int cx = L::cx(i);
-    e[i] = M(0);
-    if (cx > 0 && need_up)
-      e[i] = to_math<S, M>(__ldg(fin + (long long)i * np + n + upstream_offset(v, x, y, z, cx, L::cy(i), L::cz(i))));
-    if (cx < 0 && need_dn) {
-      const int off = wa ? upstream_offset(v, x, y, z, cx, L::cy(i), L::cz(i))
-                         : 1 + upstream_offset(v, x + 1, y, z, cx, L::cy(i), L::cz(i));
-      e[i] = to_math<S, M>(__ldg(fin + (long long)i * np + n + off));
+    for (int i = 0; i < L::Q; ++i) {
+      const int cx = L::cx(i);
+      e[i] = M(0);
+      if (cx > 0 && need_up)
+        e[i] = Units<S>::template load<M>(
+            __ldg(fin + (long long)i * np + n + upstream_offset(v, x, y, z, cx, L::cy(i), L::cz(i))));
+      if (cx < 0 && need_dn) {
+        const int off = wa ? upstream_offset(v, x, y, z, cx, L::cy(i), L::cz(i))
+                           : 1 + upstream_offset(v, x + 1, y, z, cx, L::cy(i), L::cz(i));
+        e[i] = Units<S>::template load<M>(__ldg(fin + (long long)i * np + n + off));
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      const int cx = L::cx(i);
+      const S *row = fin + (v.soff[i] + n + ro[1 - L::cy(i)][1 - L::cz(i)]);
+      e[i] = M(0);
+      if (cx > 0 && need_up) e[i] = Units<S>::template load<M>(__ldg(row - 1));
+      if (cx < 0 && need_dn) e[i] = Units<S>::template load<M>(__ldg(row + 2));
     }
   }
   M f0[L::Q], f1[L::Q];
@@ -660,21 +741,29 @@ __device__ __forceinline__ void lattice_tile_pair(const View &v, const S *__rest
       f1[i] = need_dn && !wa ? e[i] : next;
     }
   }
-  // every lane relaxes both nodes (a non-fluid node's values are discarded), so
+  // every lane relaxes both nodes (a non-fluid node's values are never read), so
   // that only the stores of pairs with a non-fluid node diverge
-  const Macro<L, M> ma = moments<L, M>(v, f0), mb = moments<L, M>(v, f1);
+  constexpr bool U = Units<S>::kStored;
+  const Macro<L, M> ma = moments<L, M, U>(v, f0), mb = moments<L, M, U>(v, f1);
   M pa[L::Q], pb[L::Q];
-  post_all<L, M, PHYS>(v, f0, ma, pa);
-  post_all<L, M, PHYS>(v, f1, mb, pb);
+  post_all<L, M, PHYS, U>(v, f0, ma, pa);
+  post_all<L, M, PHYS, U>(v, f1, mb, pb);
   if (fa && fb) {
 #pragma unroll
     for (int i = 0; i < L::Q; ++i)
       *reinterpret_cast<T *>(fout + (v.soff[i] + n)) = V::make(pa[i], pb[i]);
-  } else {
+  } else if (sa || sb) {
+    const uint32_t ka = ga ? v.amask[n] : (fa ? 0u : ~0u), kb = gb ? v.amask[n + 1] : (fb ? 0u : ~0u);
+    if (!(ka | kb)) {
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-      if (fa) fout[(long long)i * np + n] = to_store<S, M>(pa[i]);
-      if (fb) fout[(long long)i * np + n + 1] = to_store<S, M>(pb[i]);
+      for (int i = 0; i < L::Q; ++i)
+        *reinterpret_cast<T *>(fout + (v.soff[i] + n)) = V::make(pa[i], pb[i]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        if (!((ka >> i) & 1u)) fout[(long long)i * np + n] = Units<S>::template store<M>(pa[i]);
+        if (!((kb >> i) & 1u)) fout[(long long)i * np + n + 1] = Units<S>::template store<M>(pb[i]);
+      }
     }
   }
 }
@@ -773,9 +862,10 @@ __device__ __forceinline__ void fence_mbar_init() {
 
 constexpr long long kWaitLimit = 1LL << 24;  // try_wait polls before a wait counts as hung
 
-// Bounded wait on one mbarrier phase. Returns false if the limit ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-  for (long long k = 0; k < kWaitLimit; ++k)
+// Bounded wait on one mbarrier phase: at most `limit` polls. Returns false if the
+// limit ran out (limit 0 returns false at once).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit) {
+  for (long long k = 0; k < limit; ++k)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -835,29 +925,40 @@ __device__ __forceinline__ void tma_lattice(const View &v, const S *__restrict__
   if (y >= v.ny) return;  // uniform across the warp
   const int n = (z * v.ny + y) * v.nxp + x;
   const uint8_t fl = base[lay.template pops_bytes<L>() + ty * lay.W + tx];
+  const uint32_t fbal = __ballot_sync(0xffffffffu, (fl & 3) == K_FLUID);
+  if (!fbal) return;
   uint32_t bal = 0;
   if (v.bc == BC_BFL) bal = __ballot_sync(0xffffffffu, fl & F_BOUNDARY);
-  if ((fl & K_LATTICE_MASK) != K_FLUID) return;
+  const bool here = (fl & K_LATTICE_MASK) == K_FLUID;
+  const bool fill = fills_sector<S>(fl, fbal, 1);  // as in lattice_tile
+  const bool masked = __any_sync(0xffffffffu, fill);
+  if (!here && !fill) return;
   const S *pops = reinterpret_cast<const S *>(base);
   const bool xedge = x == 0 || x >= v.nx - 1;
   const int np = (int)v.np;
   M f[L::Q];
-  if (!xedge) {
+  uint32_t skip = 0;
+  if (!here) {
+    skip = v.amask[n];
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) f[i] = M(0);
+  } else if (!xedge) {
 #pragma unroll
     for (int i = 0; i < L::Q; ++i)
-      f[i] = to_math<S, M>(pops[(i * lay.H + ty) * lay.rowlen + tx + HALO - L::cx(i)]);
+      f[i] = Units<S>::template load<M>(pops[(i * lay.H + ty) * lay.rowlen + tx + HALO - L::cx(i)]);
   } else {
     Nbr nb;
     nb.init(v, x, y, z);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i)
-      f[i] = L::cx(i) == 0 ? to_math<S, M>(pops[(i * lay.H + ty) * lay.rowlen + tx + HALO])
-                           : to_math<S, M>(__ldg(fin + (long long)i * v.np + n +
-                                                 nb.at(-L::cx(i), -L::cy(i), -L::cz(i))));
+      f[i] = L::cx(i) == 0 ? Units<S>::template load<M>(pops[(i * lay.H + ty) * lay.rowlen + tx + HALO])
+                           : Units<S>::template load<M>(__ldg(fin + (long long)i * v.np + n +
+                                                              nb.at(-L::cx(i), -L::cy(i), -L::cz(i))));
   }
-  if (v.bc == BC_BFL && (fl & F_BOUNDARY)) bfl_complete<L, M>(v, *record_of(v, n, bal), f);
-  const Macro<L, M> m = moments<L, M>(v, f);
-  collide_store<L, S, M, PHYS>(v, f, m, fout + n, np);
+  if (here && v.bc == BC_BFL && (fl & F_BOUNDARY)) bfl_complete<L, M>(v, *record_of(v, n, bal), f);
+  const Macro<L, M> m = moments<L, M, Units<S>::kStored>(v, f);
+  if (masked) collide_store<L, S, M, PHYS>(v, f, m, fout + n, np, skip);
+  else collide_store<L, S, M, PHYS>(v, f, m, fout + n, np, 0u);
 }
 
 template <class L, typename S, typename M, int PHYS>
@@ -874,12 +975,16 @@ __global__ void __launch_bounds__(256, 2) k_step_tma(const View v, const S *__re
     fence_mbar_init();
   }
   __syncthreads();
+  uint32_t armed = 0;  // (warp 0) bit k: stage k has copies in flight that nobody has waited for
   if (t < 32)
     for (int j = 0; j < nstage - 1; ++j) {
       const int e = blockIdx.x + j * G;
       if (e >= v.ntiles) break;
       const int2 tl = v.tiles[e];
-      if (tl.x >= 0) tma_issue<L, S>(v, fin, tl, stages + j * stage_bytes, &bars[j], lay, t);
+      if (tl.x >= 0) {
+        tma_issue<L, S>(v, fin, tl, stages + j * stage_bytes, &bars[j], lay, t);
+        armed |= 1u << j;
+      }
     }
   uint32_t parity = 0;  // bit k: parity of the next wait on stage k
   for (int j = 0;; ++j) {
@@ -894,6 +999,7 @@ __global__ void __launch_bounds__(256, 2) k_step_tma(const View v, const S *__re
         if (tl.x >= 0) {
           fence_proxy_async_smem();  // order earlier generic accesses of the stage before the copies
           tma_issue<L, S>(v, fin, tl, stages + kn * stage_bytes, &bars[kn], lay, t);
+          armed |= 1u << kn;
         }
       }
     }
@@ -901,15 +1007,20 @@ __global__ void __launch_bounds__(256, 2) k_step_tma(const View v, const S *__re
     if (tile.x < 0) {
       boundary_tile<L, S, M>(v, fin, fout, tile, reinterpret_cast<M *>(stages + k * stage_bytes));
     } else {
-      const bool ok = mbar_wait_bounded(&bars[k], (parity >> k) & 1u);
+      const bool ok = mbar_wait_bounded(&bars[k], (parity >> k) & 1u, v.wait_limit);
       if (__syncthreads_or(!ok)) {  // the whole block leaves together
         if (t == 0) {
           atomicOr(v.err, 1);
-          for (int q = 0; q < nstage; ++q) mbar_wait_bounded(&bars[q], (parity >> q) & 1u);
+          // drain: the copies this block issued and nobody waited for complete
+          // before it leaves (they target its shared memory); only armed stages
+          // are waited on, each with the full limit
+          for (int q = 0; q < nstage; ++q)
+            if ((armed >> q) & 1u) mbar_wait_bounded(&bars[q], (parity >> q) & 1u, kWaitLimit);
         }
         return;
       }
       parity ^= 1u << k;
+      armed &= ~(1u << k);
       tma_lattice<L, S, M, PHYS>(v, fin, fout, tile, stages + k * stage_bytes, lay);
     }
     __syncthreads();  // the stage is free for the producer

@@ -108,10 +108,22 @@ __device__ __forceinline__ M dweight(int i) {
 }
 
 // ---- storage <-> math conversions (round to nearest even on store) ----
+// FP16 storage holds the shifted value times 2^14. The factor is a power of two,
+// so scaling is exact in FP32 and the rounding to FP16 is the same relative
+// rounding as without it. What it changes is the range: FP16 turns subnormal
+// below 6.1e-5, and the shifted populations of slow flows (f~ ~ w rho c.u) and a
+// weak body force's increments (~ w 3 c.F, about 1.7e-7 at |F| = 1e-6) lie far
+// below that, where subnormal spacing (6e-8) would swallow them. Scaled, values
+// down to 3.7e-9 stay normal, and |f~| up to 3.99 still fits. BF16 has the FP32
+// exponent range and needs no scaling.
+constexpr float kF16Scale = 16384.0f;
+constexpr float kF16Unscale = 1.0f / 16384.0f;
 template <typename S, typename M> __device__ __forceinline__ M to_math(S v);
 template <> __device__ __forceinline__ double to_math<double, double>(double v) { return v; }
 template <> __device__ __forceinline__ float to_math<float, float>(float v) { return v; }
-template <> __device__ __forceinline__ float to_math<__half, float>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float to_math<__half, float>(__half v) {
+  return __half2float(v) * kF16Unscale;
+}
 template <> __device__ __forceinline__ float to_math<__nv_bfloat16, float>(__nv_bfloat16 v) {
   return __bfloat162float(v);
 }
@@ -119,7 +131,9 @@ template <> __device__ __forceinline__ float to_math<__nv_bfloat16, float>(__nv_
 template <typename S, typename M> __device__ __forceinline__ S to_store(M v);
 template <> __device__ __forceinline__ double to_store<double, double>(double v) { return v; }
 template <> __device__ __forceinline__ float to_store<float, float>(float v) { return v; }
-template <> __device__ __forceinline__ __half to_store<__half, float>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __half to_store<__half, float>(float v) {
+  return __float2half_rn(v * kF16Scale);
+}
 template <> __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16, float>(float v) {
   return __float2bfloat16_rn(v);
 }
@@ -128,7 +142,10 @@ template <> __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16, flo
 // least one wall or open link (a boundary node with a record), bit 3 a fluid node
 // with a link across a thin shell (its boundary tile, not a lattice tile, relaxes
 // and stores it).
-enum : uint8_t { K_FLUID = 0, K_SOLID = 1, K_OPEN = 2, K_PAD = 3, F_BOUNDARY = 4, F_SHELL = 8 };
+// Bit 4 marks the nodes of a moving body's region: the lattice tiles never store
+// into a non-fluid node's slots there (values are written ahead into them, and
+// which ones changes every step).
+enum : uint8_t { K_FLUID = 0, K_SOLID = 1, K_OPEN = 2, K_PAD = 3, F_BOUNDARY = 4, F_SHELL = 8, F_KEEP = 16 };
 // Flag bits a lattice tile tests: it relaxes the node only when they are all zero.
 constexpr uint8_t K_LATTICE_MASK = 3 | F_SHELL;
 // Force tag of the links on the inner side of a thin shell: no force is counted there.
@@ -168,7 +185,12 @@ struct View {
   // the same scalars in FP32, so that FP32 kernels convert nothing on the
   // (slow) FP64 pipe: omega, rho0, qcut, F, omega_m
   float omega_f, rho0_f, qcut_f, F_f[3], omega_m_f;
+  // rho0 and F in the units of the stored values (times 2^14 for FP16 storage)
+  float rho0_u, F_u[3];
   const uint8_t *flags;      // [np]
+  // [np] for a non-fluid node, bit i: slot (i, n) receives a boundary value written
+  // ahead by the fluid node n + c_i (the other planes take the lattice tile's store)
+  const uint32_t *amask;
   const uint32_t *cbase;     // [np/32] records before each 32-node chunk
   const Rec *rec;            // [nb]
   const uint32_t *rnode;     // [nb] padded node index of each record
@@ -184,6 +206,7 @@ struct View {
   RecSet dyn;
   const int *dyn_count;      // device: number of records in dyn (null: no moving body)
   int *err;                  // device error word (bounded waits that ran out set bit 0)
+  long long wait_limit;      // polls before a first wait of the TMA-staged step counts as hung
 
   __host__ __device__ RecSet stat() const { return RecSet{rec, rnode, lq, luw, luw1, ltag}; }
   const void *lq;            // [nl] q of each wall link (math type)
@@ -191,18 +214,39 @@ struct View {
   const uint8_t *ltag;       // [nl] force tag of each wall link
 };
 
-// Scalar parameters in the math type of a kernel.
+// Scalar parameters in the math type of a kernel. stored_units: rho0 and F in the
+// units of the stored values (Units<S> below) instead of lattice units.
 template <typename M> struct Par;
 template <> struct Par<double> {
   double omega, rho0, qcut, F[3], omega_m;
-  __device__ __forceinline__ explicit Par(const View &v)
+  __device__ __forceinline__ explicit Par(const View &v, bool = false)
       : omega(v.omega), rho0(v.rho0), qcut(v.qcut), F{v.F[0], v.F[1], v.F[2]}, omega_m(v.omega_m) {}
 };
 template <> struct Par<float> {
   float omega, rho0, qcut, F[3], omega_m;
-  __device__ __forceinline__ explicit Par(const View &v)
-      : omega(v.omega_f), rho0(v.rho0_f), qcut(v.qcut_f), F{v.F_f[0], v.F_f[1], v.F_f[2]},
+  __device__ __forceinline__ explicit Par(const View &v, bool stored_units = false)
+      : omega(v.omega_f), rho0(stored_units ? v.rho0_u : v.rho0_f), qcut(v.qcut_f),
+        F{stored_units ? v.F_u[0] : v.F_f[0], stored_units ? v.F_u[1] : v.F_f[1],
+          stored_units ? v.F_u[2] : v.F_f[2]},
         omega_m(v.omega_m_f) {}
+};
+
+// The lattice tiles compute in the units of the stored values. For FP16 storage
+// these are the shifted populations times 2^14. With rho0 and the body force
+// scaled by the same power of two (Par with stored_units), every operation of
+// the moments and the relaxation scales exactly: the results are the lattice-unit
+// computation's times 2^14, bit for bit (FP32 neither overflows nor turns
+// subnormal at these magnitudes), and no population is multiplied on load or
+// store. The boundary tiles work in lattice units through to_math / to_store.
+template <typename S> struct Units {
+  static constexpr bool kStored = false;
+  template <typename M> __device__ static __forceinline__ M load(S v) { return to_math<S, M>(v); }
+  template <typename M> __device__ static __forceinline__ S store(M v) { return to_store<S, M>(v); }
+};
+template <> struct Units<__half> {
+  static constexpr bool kStored = true;
+  template <typename M> __device__ static __forceinline__ M load(__half v) { return __half2float(v); }
+  template <typename M> __device__ static __forceinline__ __half store(M v) { return __float2half_rn(v); }
 };
 
 // Relative element offsets of the 27 neighbours (dx, dy, dz in {-1,0,1}) of a node,

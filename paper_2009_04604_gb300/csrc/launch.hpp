@@ -41,6 +41,9 @@ cudaError_t launch_read(int lattice, int dtype, const View &v, const void *fin, 
 cudaError_t launch_force(int lattice, int dtype, const View &v, const void *cur, const void *prev,
                          const RecSet &rs, long long nrec, const int *nrec_dev, int tag, double *part,
                          const Launch &l);
+// amask[n] of every padded node (View::amask) from the node kinds in v.flags
+// (geometry.cu).
+cudaError_t launch_amask(int lattice, const View &v, uint32_t *amask, cudaStream_t s);
 cudaError_t launch_reduce_final(const double *part, long long nblocks, int ncomp, double *out,
                                 cudaStream_t s);
 

@@ -104,6 +104,8 @@ extern "C" int lbm_create(int lattice, const int dims[3], double tau, int dtype,
   cudaError_t e = cudaMalloc(&h->f[0], bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->f[1], bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->flags, np);
+  if (e == cudaSuccess) e = cudaMalloc(&h->amask, np * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->amask, 0xff, np * sizeof(uint32_t), h->stream);
   if (e == cudaSuccess) e = cudaMalloc(&h->cbase, (np / 32 + 1) * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&h->dres, 8 * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&h->err_dev, sizeof(int));
@@ -127,6 +129,47 @@ void lbm_sim::free_geometry() {
   rec = nullptr; rnode = nullptr; lq = nullptr; luw = nullptr; luw1 = nullptr; ltag = nullptr;
   nb = nl = 0;
   has_uw = 0;
+  geom_hash = 0;
+}
+
+int lbm_sim::ensure_stage_f() {
+  if (stage_f) return LBM_OK;
+  LBM_CUDA(this, cudaMalloc(&stage_f, (size_t)N * Q * sizeof(double)));
+  return LBM_OK;
+}
+
+// 64-bit FNV-1a over 8-byte words (the tail byte by byte)
+static unsigned long long fnv_words(unsigned long long h, const void *p, size_t n) {
+  const unsigned char *b = static_cast<const unsigned char *>(p);
+  size_t k = 0;
+  for (; k + 8 <= n; k += 8) {
+    unsigned long long w;
+    std::memcpy(&w, b + k, 8);
+    h = (h ^ w) * 0x100000001b3ULL;
+  }
+  for (; k < n; ++k) h = (h ^ b[k]) * 0x100000001b3ULL;
+  return h;
+}
+
+// After a static geometry is in place: the written-ahead masks of the non-fluid
+// nodes (View::amask) and the geometry's hash (for lbm_save / lbm_load).
+int lbm_sim::finish_geometry() {
+  LBM_CUDA(this, launch_amask(lattice, view(), amask, stream));
+  HostGeometry g;
+  int rc = download(g);
+  if (rc) return rc;
+  unsigned long long h = 0xcbf29ce484222325ULL;
+  const long long dims[5] = {lattice, nx, ny, nz, dtype};
+  h = fnv_words(h, dims, sizeof(dims));
+  h = fnv_words(h, g.flags.data(), g.flags.size());
+  h = fnv_words(h, g.rec.data(), g.rec.size() * sizeof(Rec));
+  h = fnv_words(h, g.rnode.data(), g.rnode.size() * sizeof(uint32_t));
+  h = fnv_words(h, g.lq.data(), g.lq.size());
+  h = fnv_words(h, g.ltag.data(), g.ltag.size());
+  h = fnv_words(h, g.luw.data(), g.luw.size());
+  h = fnv_words(h, g.luw1.data(), g.luw1.size());
+  geom_hash = h;
+  return LBM_OK;
 }
 
 void lbm_sim::drop_graphs() {
@@ -141,6 +184,7 @@ extern "C" int lbm_destroy(lbm_handle h) {
   h->free_geometry();
   cudaFree(h->f[0]); cudaFree(h->f[1]); cudaFree(h->flags); cudaFree(h->cbase);
   cudaFree(h->dres); cudaFree(h->scratch); cudaFree(h->tiles); cudaFree(h->err_dev);
+  cudaFree(h->amask); cudaFree(h->stage_f);
   h->free_moving_body();
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -173,16 +217,15 @@ extern "C" int lbm_set_options(lbm_handle h, int bc, double rho0, const double f
     return lbm_fail(h, LBM_ERR_STATE, "rho0 changes the stored shift: set it before the state");
   if (h->geom_ok && h->state_ok && (bc == LBM_BC_BFL) != (h->bc == LBM_BC_BFL)) {
     // BFL keeps a partial value in its written-ahead slots: re-encode the state
-    double *d = nullptr;
-    const size_t bytes = (size_t)h->N * h->Q * sizeof(double);
-    LBM_CUDA(h, cudaMalloc(&d, bytes));
+    int rc = h->ensure_stage_f();
+    if (rc) return rc;
+    double *d = h->stage_f;
     cudaError_t e = launch_read(h->lattice, h->dtype, h->view(), h->f[h->cur], d, nullptr, nullptr,
                                 nullptr, h->aux_shape());
     const int old_bc = h->bc;
     h->bc = bc;
     if (e == cudaSuccess) e = launch_set_pop(h->lattice, h->dtype, h->view(), h->f[h->cur], d, h->aux_shape());
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(d);
     if (e != cudaSuccess) { h->bc = old_bc; return lbm_fail(h, LBM_ERR_CUDA, cudaGetErrorString(e)); }
   }
   h->bc = bc;
@@ -239,8 +282,12 @@ View lbm_sim::view() const {
   v.omega_f = (float)v.omega; v.rho0_f = (float)rho0; v.qcut_f = (float)qcut;
   v.omega_m_f = (float)v.omega_m;
   for (int a = 0; a < 3; ++a) v.F_f[a] = (float)F[a];
-  v.flags = flags; v.cbase = cbase; v.rec = rec; v.rnode = rnode; v.nb = nb;
+  const double unit = dtype == LBM_F16 ? (double)kF16Scale : 1.0;  // stored units (lattice.cuh, Units)
+  v.rho0_u = (float)(rho0 * unit);
+  for (int a = 0; a < 3; ++a) v.F_u[a] = (float)(F[a] * unit);
+  v.flags = flags; v.amask = amask; v.cbase = cbase; v.rec = rec; v.rnode = rnode; v.nb = nb;
   v.err = err_dev;
+  v.wait_limit = wait_limit;
   v.tiles = tiles; v.gx = nxp / (step_bx * npt());
   for (int i = 0; i < Q; ++i) {
     int c[3];
@@ -355,16 +402,19 @@ extern "C" int lbm_init(lbm_handle h, double rho, const double u[3]) {
   return LBM_OK;
 }
 
+// Both calls stage the FP64 host layout in a device buffer that the handle
+// allocates on first use and keeps, so that repeated transfers never reach the
+// allocator.
 extern "C" int lbm_set_populations(lbm_handle h, const double *f) {
   if (!h || !f) return lbm_fail(h, LBM_ERR_ARG, "null argument");
   if (!h->geom_ok) return lbm_fail(h, LBM_ERR_STATE, "set the geometry first");
+  int rc = h->ensure_stage_f();
+  if (rc) return rc;
   const size_t bytes = (size_t)h->N * h->Q * sizeof(double);
-  double *d = nullptr;
-  LBM_CUDA(h, cudaMalloc(&d, bytes));
-  cudaError_t e = cudaMemcpyAsync(d, f, bytes, cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess) e = launch_set_pop(h->lattice, h->dtype, h->view(), h->f[h->cur], d, h->aux_shape());
+  cudaError_t e = cudaMemcpyAsync(h->stage_f, f, bytes, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = launch_set_pop(h->lattice, h->dtype, h->view(), h->f[h->cur], h->stage_f, h->aux_shape());
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  cudaFree(d);
   if (e != cudaSuccess) return lbm_fail(h, LBM_ERR_CUDA, cudaGetErrorString(e));
   h->state_ok = true;
   return LBM_OK;
@@ -373,14 +423,13 @@ extern "C" int lbm_set_populations(lbm_handle h, const double *f) {
 extern "C" int lbm_get_populations(lbm_handle h, double *f) {
   if (!h || !f) return lbm_fail(h, LBM_ERR_ARG, "null argument");
   if (!h->geom_ok) return lbm_fail(h, LBM_ERR_STATE, "set the geometry first");
+  int rc = h->ensure_stage_f();
+  if (rc) return rc;
   const size_t bytes = (size_t)h->N * h->Q * sizeof(double);
-  double *d = nullptr;
-  LBM_CUDA(h, cudaMalloc(&d, bytes));
-  cudaError_t e = launch_read(h->lattice, h->dtype, h->view(), h->f[h->cur], d, nullptr, nullptr,
+  cudaError_t e = launch_read(h->lattice, h->dtype, h->view(), h->f[h->cur], h->stage_f, nullptr, nullptr,
                               nullptr, h->aux_shape());
-  if (e == cudaSuccess) e = cudaMemcpyAsync(f, d, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f, h->stage_f, bytes, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  cudaFree(d);
   if (e != cudaSuccess) return lbm_fail(h, LBM_ERR_CUDA, cudaGetErrorString(e));
   return LBM_OK;
 }
@@ -552,6 +601,8 @@ int lbm_sim::upload(const HostGeometry &g) {
     }
   }
   LBM_CUDA(this, cudaStreamSynchronize(stream));
+  int rc = finish_geometry();
+  if (rc) return rc;
   geom_ok = true;
   return LBM_OK;
 }
@@ -680,5 +731,90 @@ extern "C" int lbm_autotune(lbm_handle h, int steps, int *bx, int *by, int *vari
   if (variant) *variant = best[2];
   if (tiles) *tiles = best[3];
   if (ms_per_step) *ms_per_step = best_ms / steps;
+  return LBM_OK;
+}
+
+// ---------------------------------------------------------------- save / load
+// A saved state is a header followed by the raw contents of the current
+// population buffer, byte for byte as the kernels keep them (the values written
+// ahead for the next step included), so that a resumed run continues bit for bit.
+namespace {
+struct SaveHeader {
+  char magic[8];  // "LBMSTATE"
+  uint32_t version;
+  int32_t lattice, dtype, nx, ny, nz, bc, has_body;
+  double rho0;
+  uint64_t geom_hash, body_hash;
+  int64_t pose;  // the moving body's pose index, -1 without a body
+  uint64_t pop_bytes;
+};
+constexpr uint32_t kSaveVersion = 1;
+}  // namespace
+
+extern "C" int lbm_save(lbm_handle h, void *buf, size_t *bytes) {
+  if (!h || !bytes) return lbm_fail(h, LBM_ERR_ARG, "null argument");
+  if (!h->geom_ok || !h->state_ok) return lbm_fail(h, LBM_ERR_STATE, "no state yet");
+  SaveHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, "LBMSTATE", 8);
+  hd.version = kSaveVersion;
+  hd.lattice = h->lattice; hd.dtype = h->dtype; hd.nx = h->nx; hd.ny = h->ny; hd.nz = h->nz; hd.bc = h->bc;
+  hd.has_body = h->mb.on ? 1 : 0;
+  hd.rho0 = h->rho0;
+  hd.geom_hash = h->geom_hash;
+  hd.body_hash = h->mb.on ? h->mb.hash : 0;
+  hd.pose = -1;
+  hd.pop_bytes = (uint64_t)h->Q * h->np * h->elem_size();
+  const size_t total = sizeof(SaveHeader) + hd.pop_bytes;
+  if (!buf) { *bytes = total; return LBM_OK; }
+  if (*bytes < total)
+    return lbm_fail(h, LBM_ERR_ARG, "buffer too small for the saved state: " + std::to_string(total) + " bytes needed");
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (h->mb.on) {
+    int k = 0;
+    LBM_CUDA(h, cudaMemcpy(&k, h->mb.step, sizeof(int), cudaMemcpyDeviceToHost));
+    hd.pose = k;
+  }
+  unsigned char *p = static_cast<unsigned char *>(buf);
+  std::memcpy(p, &hd, sizeof(hd));
+  LBM_CUDA(h, cudaMemcpyAsync(p + sizeof(hd), h->f[h->cur], hd.pop_bytes, cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  *bytes = total;
+  return LBM_OK;
+}
+
+extern "C" int lbm_load(lbm_handle h, const void *buf, size_t bytes) {
+  if (!h || !buf) return lbm_fail(h, LBM_ERR_ARG, "null argument");
+  if (!h->geom_ok) return lbm_fail(h, LBM_ERR_STATE, "set the same geometry first");
+  SaveHeader hd;
+  if (bytes < sizeof(hd)) return lbm_fail(h, LBM_ERR_ARG, "not a saved state: too short");
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (std::memcmp(hd.magic, "LBMSTATE", 8) != 0 || hd.version != kSaveVersion)
+    return lbm_fail(h, LBM_ERR_ARG, "not a saved state of this library version");
+  if (hd.lattice != h->lattice || hd.dtype != h->dtype || hd.nx != h->nx || hd.ny != h->ny || hd.nz != h->nz)
+    return lbm_fail(h, LBM_ERR_ARG, "the saved state has another lattice, storage type or size");
+  if (hd.bc != h->bc || hd.rho0 != h->rho0)
+    return lbm_fail(h, LBM_ERR_ARG, "the saved state has another boundary rule or reference density");
+  if (hd.geom_hash != h->geom_hash) return lbm_fail(h, LBM_ERR_ARG, "the saved state has another geometry");
+  if ((hd.has_body != 0) != h->mb.on || (h->mb.on && hd.body_hash != h->mb.hash))
+    return lbm_fail(h, LBM_ERR_ARG, "the saved state has another moving body");
+  const uint64_t pop = (uint64_t)h->Q * h->np * h->elem_size();
+  if (hd.pop_bytes != pop || bytes < sizeof(hd) + pop) return lbm_fail(h, LBM_ERR_ARG, "the saved state is truncated");
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  const unsigned char *p = static_cast<const unsigned char *>(buf);
+  LBM_CUDA(h, cudaMemcpyAsync(h->f[h->cur], p + sizeof(hd), pop, cudaMemcpyHostToDevice, h->stream));
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (h->mb.on) {
+    int rc = h->move_rebuild(hd.pose);
+    if (rc) return rc;
+  }
+  h->state_ok = true;
+  return LBM_OK;
+}
+
+extern "C" int lbm_set_wait_limit(lbm_handle h, long long polls) {
+  if (!h) return lbm_fail(nullptr, LBM_ERR_ARG, "null handle");
+  h->wait_limit = polls < 0 ? (1LL << 24) : polls;
+  h->drop_graphs();
   return LBM_OK;
 }

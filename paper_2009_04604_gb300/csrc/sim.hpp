@@ -34,6 +34,7 @@ struct MovingBody {
   int tag = 0;
   double *fpart = nullptr;         // device: per-block momentum-exchange partials of the last step
   long long nfpart = 0;            // blocks
+  unsigned long long hash = 0;     // FNV-1a of the body's shape and trajectory table
 };
 
 struct lbm_sim {
@@ -56,6 +57,7 @@ struct lbm_sim {
   void *f[2] = {nullptr, nullptr};  // population buffers; f[cur] holds the current state
   int cur = 0;
   uint8_t *flags = nullptr;
+  uint32_t *amask = nullptr;  // [np] planes of a non-fluid node that take written-ahead values
   uint32_t *cbase = nullptr;
   lbm::Rec *rec = nullptr;
   uint32_t *rnode = nullptr;
@@ -64,11 +66,14 @@ struct lbm_sim {
   long long nb = 0, nl = 0, nfluid = 0;
   int has_uw = 0;
   int has_shell = 0;  // the static geometry has links across thin shells
+  unsigned long long geom_hash = 0;  // FNV-1a of the static geometry (flags, records, link data)
 
   double *dres = nullptr;     // reduction results (device)
   int *err_dev = nullptr;     // device error word (bit 0: a bounded wait ran out)
   double *scratch = nullptr;  // per-block reduction partials (device)
   long long scratch_len = 0;
+  double *stage_f = nullptr;  // FP64 staging of lbm_set/get_populations (N*Q, device; kept)
+  long long wait_limit = 1LL << 24;  // first-wait poll limit of the TMA-staged step
 
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // captured step loops, by starting buffer
   int2 *tiles = nullptr;      // step-kernel tile table (device)
@@ -99,10 +104,13 @@ struct lbm_sim {
   int launch_steps(int n);
   int ensure_tiles();
   int move_after_step(void *fout, int set);  // body geometry for the next step (geometry.cu)
+  int move_rebuild(long long pose);          // body at pose index `pose`, records for f[cur] (geometry.cu)
   void free_moving_body();
   int capture(int parity);
   int upload(const lbm::HostGeometry &g);
   int download(lbm::HostGeometry &g);
+  int finish_geometry();  // written-ahead masks and hash of the static geometry just set
+  int ensure_stage_f();
 };
 
 int lbm_fail(lbm_sim *h, int code, const std::string &msg);

@@ -75,6 +75,9 @@ _SIGS = {
     "lbm_get_launch": [ctypes.c_void_p, _int, _int, _int, _int],
     "lbm_autotune": [ctypes.c_void_p, ctypes.c_int, _int, _int, _int, _int, _d],
     "lbm_mass_noalloc": [ctypes.c_void_p, ctypes.c_void_p],
+    "lbm_save": [ctypes.c_void_p, ctypes.c_void_p, P(ctypes.c_size_t)],
+    "lbm_load": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
+    "lbm_set_wait_limit": [ctypes.c_void_p, ctypes.c_longlong],
     "lbm_set_moving_body": [ctypes.c_void_p, P(Shape), _d, ctypes.c_int, ctypes.c_int],
     "lbm_batch_create": [P(ctypes.c_void_p), ctypes.c_int, P(ctypes.c_void_p)],
     "lbm_batch_destroy": [ctypes.c_void_p],
@@ -288,6 +291,23 @@ class Simulation:
         a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         self._ok(self.lib.lbm_get_counts(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return a.value, b.value, c.value
+
+    def save(self):
+        """The current state as bytes (lbm_save): header plus the raw stored populations."""
+        n = ctypes.c_size_t(0)
+        self._ok(self.lib.lbm_save(self.h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._ok(self.lib.lbm_save(self.h, ctypes.cast(buf, ctypes.c_void_p), ctypes.byref(n)))
+        return buf.raw[:n.value]
+
+    def load(self, blob):
+        """Restore a state written by save() into this handle (same geometry and options)."""
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        self._ok(self.lib.lbm_load(self.h, ctypes.cast(buf, ctypes.c_void_p), len(blob)))
+
+    def set_wait_limit(self, polls):
+        """Testing aid: poll limit of the TMA-staged step's first waits (negative: default)."""
+        self._ok(self.lib.lbm_set_wait_limit(self.h, int(polls)))
 
     def set_launch(self, bx, by, variant=0, tiles=4):
         self._ok(self.lib.lbm_set_launch(self.h, int(bx), int(by), int(variant), int(tiles)))
