@@ -64,7 +64,8 @@ class Shape(ctypes.Structure):
                 ("nrm", ctypes.c_double * 3), ("off", ctypes.c_double),
                 ("width", ctypes.c_double), ("period", ctypes.c_double),
                 ("v", ctypes.c_double * 3), ("om", ctypes.c_double * 3),
-                ("v1", ctypes.c_double * 3), ("om1", ctypes.c_double * 3)]
+                ("v1", ctypes.c_double * 3), ("om1", ctypes.c_double * 3),
+                ("ang", ctypes.c_double)]
 
 
 def _load():
@@ -84,6 +85,8 @@ def _load():
             lib.or_geometry.argtypes = [P(Params), u8, d, P(Shape), ctypes.c_int, u8, d, d, d, i32, u8]
             lib.or_geometry.restype = ctypes.c_long
             lib.or_bc_weights.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, d, d]
+            lib.or_torque.argtypes = [P(Params), d, i32, d, ctypes.c_int, d, d]
+            lib.or_refill_lir.argtypes = [P(Params), u8, u8, d, d, ctypes.c_int, d]
             _lib = lib
     return _lib
 
@@ -180,6 +183,16 @@ def refill(p, flags_old, flags_new, un, f):
     return f
 
 
+def refill_lir(p, flags_old, flags_new, un, fprev, f, K=5):
+    """In place: local iteration refill of the nodes that turned fluid (see
+    or_refill_lir): streamed values from upstream nodes fluid at t (post-collision
+    values of fprev), the rest from K local collide-and-bounce-back iterations."""
+    assert f.dtype == np.float64 and f.flags.c_contiguous
+    _load().or_refill_lir(ctypes.byref(p), _ptr(_c8(flags_old), ctypes.c_uint8),
+                          _ptr(_c8(flags_new), ctypes.c_uint8), _dp(_cd(un)), _dp(_cd(fprev)), int(K), _dp(f))
+    return f
+
+
 def make_shapes(specs):
     """Build a ctypes array of Shape from dicts (keys as in ``Shape``)."""
     arr = (Shape * max(1, len(specs)))()
@@ -218,6 +231,16 @@ def geometry(p, base=None, base_u=None, shapes=(), with_shell=False):
     if with_shell:
         return flags, q, uw, uw1, tag, shell
     return flags, q, uw, uw1, tag
+
+
+def torque(p, q, tag, flink, centre, want_tag=-1):
+    """Torque about ``centre`` of the link forces ``flink`` (from ``step``) of the
+    links with tag ``want_tag`` (-1: all): sum (x_W - c) x F, x_W = x_F - q c_i."""
+    T = np.zeros(3)
+    c = np.ascontiguousarray(centre, dtype=np.float64)
+    _load().or_torque(ctypes.byref(p), _dp(_cd(q)), _ptr(np.ascontiguousarray(tag, dtype=np.int32), ctypes.c_int32),
+                      _dp(_cd(flink)), int(want_tag), _dp(c), _dp(T))
+    return T
 
 
 def bc_weights(bc, q, qcut=0.01):

@@ -473,6 +473,65 @@ void or_refill(const or_params *p, const uint8_t *flags_old, const uint8_t *flag
   }
 }
 
+/* post-collision population i of a node with pre-collision populations fn (the
+ * collision of or_step: BGK with Guo forcing, or TRT) */
+static double post_one(const or_params *p, const lat_t *L, const double *fn, int i) {
+  double r, u[3];
+  moments(L, fn, p->force, &r, u);
+  const double omega = 1.0 / p->tau;
+  if (p->collision == OR_COLL_TRT) {
+    const double omega_m = 1.0 / (0.5 + p->magic / (p->tau - 0.5));
+    return trt_post(L, i, fn, r, u, p->force, omega, omega_m);
+  }
+  return fn[i] - omega * (fn[i] - feq(L, i, r, u)) + guo_source(L, i, p->tau, u, p->force);
+}
+
+/* the same collision with the node's velocity set to uw (its density from fn) */
+static double post_at(const or_params *p, const lat_t *L, const double *fn, int i, const double uw[3]) {
+  double r = 0.0;
+  for (int j = 0; j < L->Q; ++j) r += fn[j];
+  const double omega = 1.0 / p->tau;
+  if (p->collision == OR_COLL_TRT) {
+    const double omega_m = 1.0 / (0.5 + p->magic / (p->tau - 0.5));
+    return trt_post(L, i, fn, r, uw, p->force, omega, omega_m);
+  }
+  return fn[i] - omega * (fn[i] - feq(L, i, r, uw)) + guo_source(L, i, p->tau, uw, p->force);
+}
+
+void or_refill_lir(const or_params *p, const uint8_t *flags_old, const uint8_t *flags_new,
+                   const double *un, const double *fprev, int K, double *f) {
+  lat_t L;
+  if (lat_load(p->lattice, &L)) return;
+  const int Q = L.Q;
+  const int nx = p->nx, ny = p->ny;
+  const long N = (long)nx * ny * p->nz;
+  for (long n = 0; n < N; ++n) {
+    if (flags_old[n] == OR_FLUID || flags_new[n] != OR_FLUID) continue;
+    const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long)nx * ny));
+    double uw[3] = {0.0, 0.0, 0.0};
+    if (un) for (int a = 0; a < 3; ++a) uw[a] = un[n * 3 + a];
+    double fn[27];
+    int unknown[27];
+    for (int i = 0; i < Q; ++i) {
+      const long m = nbr(p, x, y, z, -L.c[i][0], -L.c[i][1], -L.c[i][2]);
+      unknown[i] = flags_old[m] != OR_FLUID;
+      fn[i] = unknown[i] ? feq(&L, i, p->rho0, uw) : post_one(p, &L, fprev + m * Q, i);
+    }
+    for (int k = 0; k < K; ++k) {
+      double r = 0.0, post[27];
+      for (int i = 0; i < Q; ++i) r += fn[i];
+      for (int i = 0; i < Q; ++i) post[i] = post_at(p, &L, fn, i, uw);
+      for (int i = 0; i < Q; ++i) {
+        if (!unknown[i]) continue;
+        double cu = 0.0;
+        for (int a = 0; a < 3; ++a) cu += L.c[i][a] * uw[a];
+        fn[i] = post[L.opp[i]] + 2.0 * L.w[i] * r * cu / CS2;
+      }
+    }
+    for (int i = 0; i < Q; ++i) f[n * Q + i] = fn[i];
+  }
+}
+
 /* ---- link geometry ---- */
 
 /* point inside the solid of shape s (ties count as solid) */
@@ -482,7 +541,10 @@ static int shape_solid(const or_shape *s, int D, const double x[3]) {
     case OR_SHAPE_SPHERE: return d0 * d0 + d1 * d1 + d2 * d2 <= s->r[0] * s->r[0];
     case OR_SHAPE_SPHERE_OUT: return d0 * d0 + d1 * d1 + d2 * d2 >= s->r[0] * s->r[0];
     case OR_SHAPE_ELLIPSOID: {
-      double t0 = d0 / s->r[0], t1 = d1 / s->r[1], t2 = D == 3 ? d2 / s->r[2] : 0.0;
+      /* offset in the body frame: rotated by -ang about z */
+      const double ca = cos(s->ang), sa = sin(s->ang);
+      const double b0 = ca * d0 + sa * d1, b1 = ca * d1 - sa * d0;
+      double t0 = b0 / s->r[0], t1 = b1 / s->r[1], t2 = D == 3 ? d2 / s->r[2] : 0.0;
       return t0 * t0 + t1 * t1 + t2 * t2 <= 1.0;
     }
     case OR_SHAPE_STRIP: {
@@ -513,6 +575,11 @@ static double shape_cross(const or_shape *s, int D, const double x[3], const int
     case OR_SHAPE_ELLIPSOID: {
       double R2 = 1.0;
       if (s->type == OR_SHAPE_ELLIPSOID) {
+        /* offset and link direction in the body frame, scaled to the unit sphere */
+        const double ca = cos(s->ang), sa = sin(s->ang);
+        const double d0 = ca * d[0] + sa * d[1], d1 = ca * d[1] - sa * d[0];
+        const double e0 = ca * e[0] + sa * e[1], e1 = ca * e[1] - sa * e[0];
+        d[0] = d0; d[1] = d1; e[0] = e0; e[1] = e1;
         for (int a = 0; a < D; ++a) { d[a] /= s->r[a]; e[a] /= s->r[a]; }
       } else {
         R2 = s->r[0] * s->r[0];
@@ -649,4 +716,29 @@ long or_geometry(const or_params *p, const uint8_t *base, const double *base_u,
     }
   }
   return ncut;
+}
+
+void or_torque(const or_params *p, const double *q, const int32_t *tag, const double *flink, int want_tag,
+               const double c[3], double T[3]) {
+  lat_t L;
+  T[0] = T[1] = T[2] = 0.0;
+  if (lat_load(p->lattice, &L)) return;
+  const int Q = L.Q;
+  const int nx = p->nx, ny = p->ny;
+  const long N = (long)nx * ny * p->nz;
+  for (long n = 0; n < N; ++n) {
+    const double X[3] = {(double)(n % nx), (double)((n / nx) % ny), (double)(n / ((long)nx * ny))};
+    for (int i = 0; i < Q; ++i) {
+      const long li = n * Q + i;
+      if (q[li] <= 0.0) continue;                       /* not a cut link */
+      if (want_tag >= 0 && tag[li] != want_tag) continue;
+      double r[3];
+      for (int a = 0; a < 3; ++a) r[a] = X[a] - q[li] * L.c[i][a] - c[a];  /* x_W - c */
+      if (L.D == 2) r[2] = 0.0;
+      const double *F = flink + li * 3;
+      T[0] += r[1] * F[2] - r[2] * F[1];
+      T[1] += r[2] * F[0] - r[0] * F[2];
+      T[2] += r[0] * F[1] - r[1] * F[0];
+    }
+  }
 }

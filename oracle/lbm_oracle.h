@@ -39,7 +39,8 @@ enum { OR_NEQ_BOUNCE_BACK = 0, OR_NEQ_REGULARIZED = 1 };
 /* Analytic shapes for the link geometry. */
 enum { OR_SHAPE_SPHERE = 0,      /* solid inside |x-c| <= r0 (circle in 2D)        */
        OR_SHAPE_SPHERE_OUT = 1,  /* solid outside |x-c| >= r0                      */
-       OR_SHAPE_ELLIPSOID = 2,   /* solid inside sum((x-c)_d/r_d)^2 <= 1 (axis-aligned) */
+       OR_SHAPE_ELLIPSOID = 2,   /* solid inside sum((x-c)'_d/r_d)^2 <= 1, with (x-c)' the offset
+                                    in the body frame: rotated by -ang about the z axis */
        OR_SHAPE_STRIP = 3,       /* fluid strip |nrm.x - off| < width/2, periodic along nrm
                                     with period 'period' (0 = not periodic); solid elsewhere */
        OR_SHAPE_SHELL = 4 };     /* thin spherical shell |x-c| = r0 (a circle in 2D) with fluid
@@ -75,6 +76,8 @@ typedef struct {
   double off, width, period;   /* strip: centre-line offset, width, normal period */
   double v[3], om[3];          /* rigid velocity and angular velocity at time t */
   double v1[3], om1[3];        /* the same at time t + 1 */
+  double ang;                  /* ellipsoid: rotation about the z axis (radians); its
+                                  semi-axes r[0], r[1] lie along (cos, sin) and (-sin, cos) */
 } or_shape;
 
 /* Lattice tables in the oracle's own order: c[i*3 + d], w[i], opp[i]. Returns Q. */
@@ -110,6 +113,24 @@ double or_mass(const or_params *p, const uint8_t *flags, const double *f);
 void or_refill(const or_params *p, const uint8_t *flags_old, const uint8_t *flags_new,
                const double *un, double *f);
 
+/* Local iteration refill (App. D, modified LIR; the paper gives it as a figure:
+ * this is the reading the library follows). A node that is not fluid in
+ * flags_old and fluid in flags_new (a fresh node) gets, for each direction i:
+ *   - when its upstream node x - c_i was fluid at t: the post-collision value
+ *     f*_i(x - c_i, t) computed from fprev, the state at t (what the step would
+ *     have streamed to it);
+ *   - otherwise: the value found by K local iterations of collide and bounce
+ *     back at the node, which start from f^eq_i(rho0, un[n]) and then set the
+ *     unknown f_i to the node's own post-collision f*_ibar plus the moving-wall
+ *     term 2 w_i rho c_i.un[n] / c_s^2. The fluid at a fresh node moves with the
+ *     body: the local collision is the step's (BGK or TRT, with the body force)
+ *     at the node's density and the velocity un[n]. With the velocity held, each
+ *     iteration contracts the error by |1 - 1/tau| or better (with the node's
+ *     own velocity, bounce-back would flip its momentum every iteration).
+ * f is the state at t+1, changed in place at fresh nodes only. */
+void or_refill_lir(const or_params *p, const uint8_t *flags_old, const uint8_t *flags_new,
+                   const double *un, const double *fprev, int K, double *f);
+
 /* Link geometry from analytic shapes.
  *   base: caller flags (walls, inlet, outlet); a fluid base node inside any shape
  *   becomes solid. Links cut by a base-flag node get q = 1/2 and the wall
@@ -126,6 +147,13 @@ void or_refill(const or_params *p, const uint8_t *flags_old, const uint8_t *flag
 long or_geometry(const or_params *p, const uint8_t *base, const double *base_u,
                  const or_shape *shapes, int nshapes, uint8_t *flags, double *q,
                  double *uw, double *uw1, int32_t *tag, uint8_t *shell);
+
+/* Torque about the point c of the momentum exchange (flink from or_step) of the
+ * links with the given tag (tag < 0: every wall link): T = sum (x_W - c) x F_link,
+ * with x_W = x_F - q c_i the link's wall point (Sec. II.F; the moment of the
+ * link forces of Eq. force-boundary-node). q and tag as or_geometry writes them. */
+void or_torque(const or_params *p, const double *q, const int32_t *tag, const double *flink, int want_tag,
+               const double c[3], double T[3]);
 
 /* Interpolation weights the boundary rule applies to its points, for tests:
  * writes up to 3 (s, a) pairs for the scheme at this q and returns their count. */
