@@ -87,7 +87,8 @@ enum lbm_status {
 enum lbm_shape_type {
   LBM_SHAPE_SPHERE = 0,     /* solid inside |x - c| <= r[0] (a circle on D2Q9)            */
   LBM_SHAPE_SPHERE_OUT = 1, /* solid outside |x - c| >= r[0]                               */
-  LBM_SHAPE_ELLIPSOID = 2,  /* solid inside sum_d ((x - c)_d / r[d])^2 <= 1, axis-aligned  */
+  LBM_SHAPE_ELLIPSOID = 2,  /* solid inside sum_d ((x - c)'_d / r[d])^2 <= 1, (x - c)' the
+                               offset turned by -ang about the z axis (ang = 0: axis-aligned) */
   LBM_SHAPE_STRIP = 3,      /* fluid where |v| < width/2, with v = nrm.x - off. When
                                period > 0, v is first wrapped into [-period/2, period/2) */
   LBM_SHAPE_SHELL = 4       /* thin spherical shell |x - c| = r[0] >= 1 (a circle on D2Q9)
@@ -102,6 +103,8 @@ typedef struct {
   double off, width, period;/* strip parameters */
   double v[3], om[3];       /* rigid velocity, angular velocity at time t */
   double v1[3], om1[3];     /* the same at time t+1 (wall population at s = 0) */
+  double ang;               /* ellipsoid: rotation about the z axis (radians); its semi-axes
+                               r[0], r[1] lie along (cos ang, sin ang) and (-sin ang, cos ang) */
 } lbm_shape;
 
 /* Lattice tables in this library's direction order: c[i*3 + d], w[i].
@@ -189,13 +192,52 @@ int lbm_build_geometry(lbm_handle h, const uint8_t *base, const double *base_u,
  * (the link-geometry kernel, restricted to a region box that covers the whole
  * trajectory): node kinds, q and u_w = v + om x (x_W - c) at the new pose, and
  * u_w at the following pose for the wall population at s = 0 (Sec. II.D-II.E).
- * A node that turns fluid gets f^eq(rho0, u_body) (the paper refills by local
- * iterations, App. D). A node that turns solid is dropped. The region, widened
+ * A node that turns fluid is refilled (lbm_set_refill: f^eq(rho0, u_body) by
+ * default, or the local iteration refill of App. D). A node that turns solid is
+ * dropped. The region, widened
  * by one node, must lie inside the lattice and hold only fluid nodes of the
  * static geometry; otherwise LBM_ERR_ARG. BFL is not available with a moving
  * body. Call after lbm_build_geometry/lbm_set_geometry; a new static geometry
  * removes the body. lbm_wall_force includes the body's links (its tag). */
 int lbm_set_moving_body(lbm_handle h, const lbm_shape *body, const double *traj, int ntraj, int t0);
+
+/* A rigid body turning freely about the z axis through its centre under the
+ * fluid's torque, the coupling of Sec. III.C (Jeffery's orbit): a sphere or an
+ * ellipsoid (body->type, c, r, ang = initial rotation about z, om[2] = initial
+ * angular velocity, tag). inertia: its moment of inertia about that axis, in
+ * lattice units (mass x length^2; per unit length on D2Q9). After every step the
+ * library reduces, on the device and in FP64, the torque T about the centre of
+ * the momentum exchange of the body's links (as lbm_wall_torque), then turns the
+ * body: omega += T / inertia, angle += omega (semi-implicit Euler, unit time
+ * step), and rebuilds its link geometry at the new angle, with wall velocity
+ * omega x (x_W - c) at t and t+1 alike (the next torque is not known yet). Nodes
+ * it uncovers are refilled as for lbm_set_moving_body. The centre does not move.
+ * history: number of steps of (angle, omega, torque) kept on the device (read
+ * with lbm_get_body_history). The same conditions as lbm_set_moving_body apply to
+ * the region the body sweeps (a disc of its largest in-plane semi-axis). */
+int lbm_set_free_body(lbm_handle h, const lbm_shape *body, double inertia, int history);
+
+/* The last min(*n, steps taken, history) entries of a free body's history, in
+ * step order: out[3*k + {0, 1, 2}] = angle and angular velocity after the step,
+ * and the torque of the step. out NULL: writes the number available into *n.
+ * Synchronises. LBM_ERR_STATE without a free body. */
+int lbm_get_body_history(lbm_handle h, double *out, int64_t *n);
+
+/* Refill of the nodes a moving or free body uncovers (fresh nodes):
+ *   REFILL_EQUILIBRIUM (default): every population of a fresh node becomes
+ *     f^eq_i(rho0, u_b), u_b the body's velocity at the node;
+ *   REFILL_LIR: local iteration refill, the reading of the paper's modified LIR
+ *     (App. D, given there as a figure): the populations streamed to the node
+ *     from upstream nodes that were fluid are kept; the others are found by
+ *     `iterations` local iterations of collide-and-bounce-back at the node,
+ *     from f^eq(rho0, u_b), colliding at the node's density and the velocity
+ *     u_b and bouncing back the node's own post-collision values with the
+ *     moving-wall term. Each iteration contracts the error by about |1 - 1/tau|
+ *     or better; nodes with few streamed values converge slowest.
+ * Applies to the body set now and to bodies set later. LBM_ERR_ARG for an unknown
+ * mode or iterations outside 0..100000. */
+enum lbm_refill { LBM_REFILL_EQUILIBRIUM = 0, LBM_REFILL_LIR = 1 };
+int lbm_set_refill(lbm_handle h, int mode, int iterations);
 
 /* Equilibrium start f = f^eq(rho, u) on every fluid node. */
 int lbm_init(lbm_handle h, double rho, const double u[3]);
@@ -224,6 +266,14 @@ int lbm_macros(lbm_handle h, double *rho, double *u);
  * value written from the other side): it is computed again from the state the
  * last step read, so call this right after a step. */
 int lbm_wall_force(lbm_handle h, int tag, double F[3]);
+
+/* Torque about the point centre[3] of the momentum exchange of the last step
+ * (Sec. II.F): the sum over the static geometry's wall links with this tag (-1:
+ * every tag) of (x_W - centre) x F_link, where F_link is the link's term of
+ * lbm_wall_force and x_W = x_F - q c_i the link's wall point. FP64, fixed order,
+ * deterministic. Synchronises the stream. A free body's own torque is in
+ * lbm_get_body_history. */
+int lbm_wall_torque(lbm_handle h, int tag, const double centre[3], double T[3]);
 
 /* Total mass sum of rho over the fluid nodes, in FP64. Deterministic. Synchronises.
  * Returns LBM_ERR_NONFINITE if the sum is NaN or Inf. */

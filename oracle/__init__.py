@@ -243,6 +243,47 @@ def torque(p, q, tag, flink, centre, want_tag=-1):
     return T
 
 
+def free_rotation(p, base, base_u, body, inertia, f0, steps, lir=0):
+    """A rigid body turning freely about the z axis through its centre (the
+    Jeffery's-orbit test of Sec. III.C), coupled to the fluid one step at a time:
+    step the fluid with the body's links at the current angle (wall velocity
+    omega x (x_W - c)), take the torque of that step's link forces (torque), turn
+    the body by the semi-implicit Euler update omega += T / I, angle += omega, rebuild
+    its links at the new angle, and refill the nodes it uncovered at the body
+    velocity (refill, or refill_lir with ``lir`` iterations, App. D). ``body`` is
+    a shape dict (SHAPE_ELLIPSOID or SHAPE_SPHERE) with keys c, r, tag and ang.
+    Returns (flags, f, history) with history[k] = (angle, omega, torque) after step k+1."""
+    c = np.asarray(body["c"], dtype=np.float64)
+    ang, om = float(body.get("ang", 0.0)), 0.0
+
+    def links(a, w):
+        return geometry(p, base, base_u, [dict(body, ang=a, om=(0.0, 0.0, w), om1=(0.0, 0.0, w))])
+
+    flags, q, uw, uw1, tag = links(ang, om)
+    f = _cd(f0).copy()
+    X = np.arange(flags.size)
+    nx, ny = p.nx, p.ny
+    rx = X % nx - c[0]
+    ry = (X // nx) % ny - c[1]
+    hist = np.zeros((steps, 3))
+    for k in range(steps):
+        fprev = f
+        f, flink = step(p, flags, f, q, uw, uw1, want_force=True)
+        T = torque(p, q, tag, flink, c, int(body["tag"]))[2]
+        om += T / inertia
+        ang += om
+        fn, qn, uwn, uw1n, tagn = links(ang, om)
+        un = np.zeros((flags.size, 3))
+        un[:, 0], un[:, 1] = -om * ry, om * rx      # omega e_z x (x - c)
+        if lir:
+            refill_lir(p, flags, fn, un, fprev, f, K=lir)
+        else:
+            refill(p, flags, fn, un, f)
+        flags, q, uw, uw1, tag = fn, qn, uwn, uw1n, tagn
+        hist[k] = (ang, om, T)
+    return flags, f, hist
+
+
 def bc_weights(bc, q, qcut=0.01):
     """``[(s_j, a_j)]`` the boundary rule interpolates through at this q."""
     s = np.zeros(3)

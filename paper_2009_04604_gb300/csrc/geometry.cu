@@ -39,7 +39,14 @@ struct GeoShape {
   double c[3], r[3], nrm[3];
   double off, width, period;
   double v[3], om[3], v1[3], om1[3];
+  double ca, sa;  // ellipsoid: cos and sin of its rotation about the z axis
 };
+
+// rotation of a shape about z, as its cosine and sine
+__host__ __device__ inline void set_rotation(GeoShape &s, double ang) {
+  s.ca = cos(ang);
+  s.sa = sin(ang);
+}
 
 struct GeoView {
   View v;
@@ -65,7 +72,9 @@ __device__ bool shape_solid(const GeoShape &s, int D, double x0, double x1, doub
     case LBM_SHAPE_SPHERE: return d0 * d0 + d1 * d1 + d2 * d2 <= s.r[0] * s.r[0];
     case LBM_SHAPE_SPHERE_OUT: return d0 * d0 + d1 * d1 + d2 * d2 >= s.r[0] * s.r[0];
     case LBM_SHAPE_ELLIPSOID: {
-      const double t0 = d0 / s.r[0], t1 = d1 / s.r[1], t2 = D == 3 ? d2 / s.r[2] : 0.0;
+      // the offset in the body frame: turned by -ang about z
+      const double b0 = s.ca * d0 + s.sa * d1, b1 = s.ca * d1 - s.sa * d0;
+      const double t0 = b0 / s.r[0], t1 = b1 / s.r[1], t2 = D == 3 ? d2 / s.r[2] : 0.0;
       return t0 * t0 + t1 * t1 + t2 * t2 <= 1.0;
     }
     case LBM_SHAPE_STRIP: {
@@ -104,6 +113,10 @@ __device__ double shape_cross(const GeoShape &s, int D, const double x[3], const
   }
   double R2 = 1.0;
   if (s.type == LBM_SHAPE_ELLIPSOID) {
+    // offset and link direction in the body frame, scaled to the unit sphere
+    const double d0 = s.ca * d[0] + s.sa * d[1], d1 = s.ca * d[1] - s.sa * d[0];
+    const double e0 = s.ca * e[0] + s.sa * e[1], e1 = s.ca * e[1] - s.sa * e[0];
+    d[0] = d0; d[1] = d1; e[0] = e0; e[1] = e1;
     for (int a = 0; a < D; ++a) { d[a] = d[a] / s.r[a]; e[a] = e[a] / s.r[a]; }
   } else {
     R2 = s.r[0] * s.r[0];
@@ -428,7 +441,9 @@ void exclusive_scan(uint32_t *a, long long n, uint32_t *tot, uint32_t *total, cu
 static void shape_box(const lbm_shape &s, int D, double lo[3], double hi[3], bool &bounded) {
   bounded = s.type == LBM_SHAPE_SPHERE || s.type == LBM_SHAPE_ELLIPSOID || s.type == LBM_SHAPE_SHELL;
   for (int a = 0; a < 3; ++a) {
-    const double r = s.type == LBM_SHAPE_ELLIPSOID ? s.r[a] : s.r[0];
+    // a rotated ellipsoid stays inside max(r[0], r[1]) in x and y
+    const double rxy = s.r[0] > s.r[1] ? s.r[0] : s.r[1];
+    const double r = s.type == LBM_SHAPE_ELLIPSOID ? (a < 2 && s.ang != 0.0 ? rxy : s.r[a]) : s.r[0];
     lo[a] = (a < D) ? s.c[a] - r - 2.0 : -1e300;
     hi[a] = (a < D) ? s.c[a] + r + 2.0 : 1e300;
   }
@@ -499,6 +514,7 @@ extern "C" int lbm_build_geometry(lbm_handle h, const uint8_t *base, const doubl
       if (s.v[a] != 0.0 || s.om[a] != 0.0 || s.v1[a] != 0.0 || s.om1[a] != 0.0) moving = true;
     }
     o.off = s.off; o.width = s.width; o.period = s.period;
+    set_rotation(o, s.type == LBM_SHAPE_ELLIPSOID ? s.ang : 0.0);
   }
   if (base && base_u)
     for (long long n = 0; n < h->N && !moving; ++n)
@@ -646,12 +662,25 @@ struct MoveGeo {
   const double *traj;      // [ntraj][9]
   int ntraj;
   const int *step;         // current pose index
+  const double *state;     // free body: [angle, omega, centre, inertia] (null: traj)
   int ox, oy, oz, rx, ry, rz;
   long long rsize;
 };
 
 __device__ __forceinline__ GeoShape body_at(const MoveGeo &g, int k) {
   GeoShape s = *g.shape;
+  if (g.state) {
+    // free rotation about z through the fixed centre; the wall velocity at t+1 is
+    // taken as the current one (the torque of the next step is not known yet)
+    const double ang = g.state[0], om = g.state[1];
+    for (int a = 0; a < 3; ++a) {
+      s.c[a] = g.state[2 + a];
+      s.v[a] = s.v1[a] = 0.0;
+      s.om[a] = s.om1[a] = a == 2 ? om : 0.0;
+    }
+    set_rotation(s, ang);
+    return s;
+  }
   const double *p = g.traj + 9LL * (k % g.ntraj);
   const double *p1 = g.traj + 9LL * ((k + 1) % g.ntraj);
   for (int a = 0; a < 3; ++a) {
@@ -695,6 +724,98 @@ __global__ void k_move_update(const MoveGeo g, int koff, int refill, uint8_t *__
           to_store<S, M>(feq_s<L, M>(i, M(0), M(v.rho0), ux, uy, uz, usq));
   }
   flags[n] = now | F_KEEP;  // the lattice tiles never store into the region's non-fluid slots
+}
+
+// Local iteration refill (LIR), in three launches so that the neighbours' kinds
+// at t are still in `flags` while fresh nodes are refilled:
+//  1. k_move_kinds: the region's kinds at the new pose into nkind;
+//  2. k_move_lir: every fresh node (not fluid at t, fluid at t+1) keeps the
+//     values streamed to it from upstream nodes that were fluid at t (already in
+//     its gather slots: those nodes' own post-collision stores), and finds the
+//     others by `iters` local iterations of collide-and-bounce-back: start from
+//     f^eq_i(rho0, u_b); collide at the node's density and the body velocity u_b
+//     (the step's collision, with the body force); set each unknown f_i to the
+//     node's post-collision f*_ibar plus 2 w_i rho c_i.u_b / c_s^2. The results
+//     go into the gather slots of the unknown directions, which belong to nodes
+//     that were the body's at t (never stored into by the lattice tiles);
+//  3. k_move_commit: the new kinds into flags.
+// The paper applies its modified LIR before the global collide and stream (App.
+// D); here it runs at the end of step t, which comes to the same: before the
+// collide and stream of step t+1.
+template <class L>
+__global__ void k_move_kinds(const MoveGeo g, int koff, uint8_t *__restrict__ nkind) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= g.rsize) return;
+  int x, y, z;
+  region_xyz(g, r, x, y, z);
+  const GeoShape b = body_at(g, *g.step + koff);
+  nkind[r] = shape_solid(b, g.D, (double)x, (double)y, (double)z) ? K_SOLID : K_FLUID;
+}
+
+template <class L, typename S, typename M>
+__global__ void k_move_lir(const MoveGeo g, int koff, int iters, const uint8_t *__restrict__ flags,
+                           const uint8_t *__restrict__ nkind, S *__restrict__ fout) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= g.rsize) return;
+  int x, y, z;
+  region_xyz(g, r, x, y, z);
+  const View &v = g.v;
+  const int n = (z * v.ny + y) * v.nxp + x;
+  if ((flags[n] & 3) == K_FLUID || nkind[r] != K_FLUID) return;  // not a fresh node
+  const GeoShape b = body_at(g, *g.step + koff);
+  const double rx_ = x - b.c[0], ry_ = y - b.c[1], rz_ = g.D == 3 ? z - b.c[2] : 0.0;
+  double ub[3] = {b.v[0] + b.om[1] * rz_ - b.om[2] * ry_, b.v[1] + b.om[2] * rx_ - b.om[0] * rz_,
+                  b.v[2] + b.om[0] * ry_ - b.om[1] * rx_};
+  if (g.D == 2) ub[2] = 0.0;
+  using X = Ex<M>;
+  const Par<M> P(v);
+  const M ux = M(ub[0]), uy = M(ub[1]), uz = M(ub[2]);
+  const M usq = X::fma(uz, uz, X::fma(uy, uy, X::mul(ux, ux)));
+  Nbr nb;
+  nb.init(v, x, y, z);
+  M f[L::Q];
+  uint32_t unknown = 0;
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    const int off = nb.at(-L::cx(i), -L::cy(i), -L::cz(i));
+    if ((flags[n + off] & 3) == K_FLUID) {
+      f[i] = to_math<S, M>(fout[(long long)i * v.np + n + off]);
+    } else {
+      unknown |= 1u << i;
+      f[i] = feq_r<L, M>(i, M(0), P.rho0, ux, uy, uz, usq);
+    }
+  }
+  for (int k = 0; k < iters; ++k) {
+    Macro<L, M> m;
+    M d = M(0);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) d = X::add(d, f[i]);
+    m.drho = d;
+    m.rho = X::add(P.rho0, d);
+    m.ux = ux; m.uy = uy; m.uz = uz; m.usq = usq;
+    M post[L::Q];
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) post[i] = post_r<L, M>(v, P, i, f[i], f[opp<L>(i)], m);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+      if ((unknown >> i) & 1u) {
+        const M me = X::mul(X::mul(X::mul(M(6), M(weight<L>(i))), m.rho), cdot_r<L, M>(i, ux, uy, uz));
+        f[i] = X::add(post[opp<L>(i)], me);
+      }
+  }
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i)
+    if ((unknown >> i) & 1u)
+      fout[(long long)i * v.np + n + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))] = to_store<S, M>(f[i]);
+}
+
+__global__ void k_move_commit(const MoveGeo g, const uint8_t *__restrict__ nkind, uint8_t *__restrict__ flags) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= g.rsize) return;
+  int x, y, z;
+  region_xyz(g, r, x, y, z);
+  const View &v = g.v;
+  flags[(z * v.ny + y) * v.nxp + x] = nkind[r] | F_KEEP;
 }
 
 // per 32-node region chunk: records and wall links (the region's fluid nodes whose
@@ -796,6 +917,30 @@ __global__ void k_move_fill(const MoveGeo g, int koff, const uint8_t *__restrict
 
 __global__ void k_move_advance(int *step) { *step += 1; }
 
+// Free body: the torque of the step just taken (sum of the per-block partials, z
+// component, in a fixed order) turns the body about z: omega += T / I, then
+// angle += omega (semi-implicit Euler, unit time step). History entry `*step`
+// records angle, omega and torque. One warp.
+__global__ void k_body_rotate(const double *__restrict__ tpart, long long nblk, double *__restrict__ state,
+                              double *__restrict__ hist, int cap, const int *__restrict__ step) {
+  const int lane = threadIdx.x;
+  double t = 0.0;
+  for (long long b = lane; b < nblk; b += 32) t += tpart[b * 3 + 2];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) {
+    const double om = state[1] + t / state[5];
+    const double ang = state[0] + om;
+    state[0] = ang;
+    state[1] = om;
+    if (cap > 0) {
+      const long long k = *step % cap;
+      hist[3 * k] = ang;
+      hist[3 * k + 1] = om;
+      hist[3 * k + 2] = t;
+    }
+  }
+}
+
 template <class Fn>
 static cudaError_t move_dispatch(int lattice, int dtype, Fn &&fn) {
   if (lattice == 0) {
@@ -832,13 +977,21 @@ static cudaError_t move_geometry(lbm_sim *h, int koff, int refill, void *fout, i
   g.traj = mb.traj;
   g.ntraj = mb.ntraj;
   g.step = mb.step;
+  g.state = mb.free_rot ? mb.state : nullptr;
   g.ox = mb.ox; g.oy = mb.oy; g.oz = mb.oz; g.rx = mb.rx; g.ry = mb.ry; g.rz = mb.rz;
   g.rsize = mb.rsize;
   cudaStream_t st = h->stream;
   const unsigned blocks = (unsigned)((mb.rpad + 255) / 256);
   const long long nchunk = mb.rpad / 32;
   return move_dispatch(h->lattice, h->dtype, [&]<class L, typename S, typename M>() {
-    k_move_update<L, S, M><<<blocks, 256, 0, st>>>(g, koff, refill, h->flags, static_cast<S *>(fout));
+    if (refill && mb.refill_mode == LBM_REFILL_LIR) {
+      k_move_kinds<L><<<blocks, 256, 0, st>>>(g, koff, mb.nkind);
+      k_move_lir<L, S, M><<<blocks, 256, 0, st>>>(g, koff, mb.refill_iters, h->flags, mb.nkind,
+                                                  static_cast<S *>(fout));
+      k_move_commit<<<blocks, 256, 0, st>>>(g, mb.nkind, h->flags);
+    } else {
+      k_move_update<L, S, M><<<blocks, 256, 0, st>>>(g, koff, refill, h->flags, static_cast<S *>(fout));
+    }
     k_move_count<L><<<blocks, 256, 0, st>>>(g, h->flags, mb.crec, mb.clink, mb.rpad);
     exclusive_scan(mb.crec, nchunk, mb.tot, reinterpret_cast<uint32_t *>(mb.count[set]), st);
     exclusive_scan(mb.clink, nchunk, mb.tot, mb.totals, st);
@@ -862,7 +1015,12 @@ int lbm_sim::move_after_step(void *fout, int set) {
   lf.grid = dim3((unsigned)mb.nfpart);
   lf.block = dim3(256);
   lf.stream = stream;
-  cudaError_t e = launch_force(lattice, dtype, view(), fout, nullptr, rs, 0, mb.count[s], -1, mb.fpart, lf);
+  cudaError_t e = launch_force(lattice, dtype, view(), fout, nullptr, rs, 0, mb.count[s], -1, mb.fpart, lf,
+                               mb.free_rot ? mb.tpart : nullptr, mb.centre[0], mb.centre[1], mb.centre[2]);
+  if (e == cudaSuccess && mb.free_rot) {
+    k_body_rotate<<<1, 32, 0, stream>>>(mb.tpart, mb.nfpart, mb.state, mb.hist, mb.hist_cap, mb.step);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = move_geometry(this, 1, 1, fout, set);
   if (e == cudaSuccess) {
     k_move_advance<<<1, 1, 0, stream>>>(mb.step);
@@ -885,6 +1043,7 @@ void lbm_sim::free_moving_body() {
   if (!mb.on && !mb.traj) return;
   cudaStreamSynchronize(stream);
   cudaFree(mb.shape); cudaFree(mb.traj); cudaFree(mb.step); cudaFree(mb.fpart);
+  cudaFree(mb.state); cudaFree(mb.tpart); cudaFree(mb.hist); cudaFree(mb.nkind);
   cudaFree(mb.crec); cudaFree(mb.clink); cudaFree(mb.tot); cudaFree(mb.totals);
   for (int k = 0; k < 2; ++k) {
     cudaFree(mb.rec[k]); cudaFree(mb.rnode[k]); cudaFree(mb.lq[k]); cudaFree(mb.luw[k]); cudaFree(mb.luw1[k]);
@@ -895,25 +1054,14 @@ void lbm_sim::free_moving_body() {
   drop_graphs();
 }
 
-extern "C" int lbm_set_moving_body(lbm_handle h, const lbm_shape *body, const double *traj, int ntraj, int t0) {
-  if (!h || !body || !traj) return lbm_fail(h, LBM_ERR_ARG, "null argument");
-  if (!h->geom_ok) return lbm_fail(h, LBM_ERR_STATE, "build the static geometry first");
-  if (h->has_shell) return lbm_fail(h, LBM_ERR_ARG, "a moving body cannot share a geometry with thin shells");
-  if (body->type != LBM_SHAPE_SPHERE && body->type != LBM_SHAPE_ELLIPSOID)
-    return lbm_fail(h, LBM_ERR_ARG, "a moving body is a sphere or an ellipsoid");
-  if (body->tag < 0 || body->tag > 7) return lbm_fail(h, LBM_ERR_ARG, "tags must be 0..7");
-  if (ntraj < 2 || t0 < 0) return lbm_fail(h, LBM_ERR_ARG, "the trajectory needs at least two poses");
-  if (h->bc == LBM_BC_BFL) return lbm_fail(h, LBM_ERR_ARG, "BFL cannot be used with a moving body");
+// Region, buffers and first geometry of a moving body (prescribed trajectory,
+// or free rotation when free_state is not null). lo/hi: the box the body's
+// centre covers; ext: the body's half-extent along each axis.
+static int setup_body(lbm_handle h, const lbm_shape *body, const double lo[3], const double hi[3],
+                      const double ext[3], const double *traj, int ntraj, int t0, const double *free_state,
+                      int history) {
   const int D = h->lattice == LBM_D2Q9 ? 2 : 3;
-  double ext[3];
-  for (int a = 0; a < 3; ++a) ext[a] = body->type == LBM_SHAPE_ELLIPSOID ? body->r[a] : body->r[0];
-  // region: the trajectory's bounding box, widened by the body and two links
-  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-  for (int k = 0; k < ntraj; ++k)
-    for (int a = 0; a < 3; ++a) {
-      lo[a] = std::min(lo[a], traj[9 * k + a]);
-      hi[a] = std::max(hi[a], traj[9 * k + a]);
-    }
+  // region: the box widened by the body and two links
   const int dims[3] = {h->nx, h->ny, h->nz};
   int o[3], e[3];
   for (int a = 0; a < 3; ++a) {
@@ -950,6 +1098,7 @@ extern "C" int lbm_set_moving_body(lbm_handle h, const lbm_shape *body, const do
   gs.type = body->type;
   gs.tag = body->tag;
   for (int a = 0; a < 3; ++a) gs.r[a] = body->r[a];
+  set_rotation(gs, body->type == LBM_SHAPE_ELLIPSOID ? body->ang : 0.0);
   const size_t ls = h->link_size();
   const long long nchunk = mb.rpad / 32;
   LBM_CUDA_GEO(h, cudaMalloc(&mb.shape, sizeof(GeoShape)));
@@ -961,6 +1110,9 @@ extern "C" int lbm_set_moving_body(lbm_handle h, const lbm_shape *body, const do
   LBM_CUDA_GEO(h, cudaMalloc(&mb.clink, sizeof(uint32_t) * (nchunk + 1)));
   LBM_CUDA_GEO(h, cudaMalloc(&mb.tot, sizeof(uint32_t) * ((nchunk + 1023) / 1024 + 1)));
   LBM_CUDA_GEO(h, cudaMalloc(&mb.totals, sizeof(uint32_t) * 2));
+  LBM_CUDA_GEO(h, cudaMalloc(&mb.nkind, mb.rpad));
+  mb.refill_mode = h->refill_mode;
+  mb.refill_iters = h->refill_iters;
   for (int k = 0; k < 2; ++k) {
     LBM_CUDA_GEO(h, cudaMalloc(&mb.rec[k], sizeof(Rec) * mb.cap_rec));
     LBM_CUDA_GEO(h, cudaMalloc(&mb.rnode[k], sizeof(uint32_t) * mb.cap_rec));
@@ -974,20 +1126,33 @@ extern "C" int lbm_set_moving_body(lbm_handle h, const lbm_shape *body, const do
   LBM_CUDA_GEO(h, cudaMemcpyAsync(mb.shape, &gs, sizeof(GeoShape), cudaMemcpyHostToDevice, h->stream));
   LBM_CUDA_GEO(h, cudaMemcpyAsync(mb.traj, traj, sizeof(double) * 9 * ntraj, cudaMemcpyHostToDevice, h->stream));
   LBM_CUDA_GEO(h, cudaMemcpyAsync(mb.step, &t0, sizeof(int), cudaMemcpyHostToDevice, h->stream));
-  {  // identity of the body for lbm_save / lbm_load
-    unsigned long long hh = 0xcbf29ce484222325ULL;
+  unsigned long long hh = 0xcbf29ce484222325ULL;  // identity of the body for lbm_save / lbm_load
+  {
     const unsigned char *pb = reinterpret_cast<const unsigned char *>(&gs);
     for (size_t k = 0; k < sizeof(GeoShape); ++k) hh = (hh ^ pb[k]) * 0x100000001b3ULL;
     const unsigned char *pt = reinterpret_cast<const unsigned char *>(traj);
     for (size_t k = 0; k < sizeof(double) * 9 * (size_t)ntraj; ++k) hh = (hh ^ pt[k]) * 0x100000001b3ULL;
-    mb.hash = hh;
   }
+  if (free_state) {
+    mb.free_rot = true;
+    for (int a = 0; a < 3; ++a) mb.centre[a] = free_state[2 + a];
+    mb.hist_cap = history;
+    LBM_CUDA_GEO(h, cudaMalloc(&mb.state, sizeof(double) * 6));
+    LBM_CUDA_GEO(h, cudaMemcpyAsync(mb.state, free_state, sizeof(double) * 6, cudaMemcpyHostToDevice, h->stream));
+    LBM_CUDA_GEO(h, cudaMalloc(&mb.tpart, sizeof(double) * 3 * mb.nfpart));
+    LBM_CUDA_GEO(h, cudaMemsetAsync(mb.tpart, 0, sizeof(double) * 3 * mb.nfpart, h->stream));
+    LBM_CUDA_GEO(h, cudaMalloc(&mb.hist, sizeof(double) * 3 * std::max(1, history)));
+    LBM_CUDA_GEO(h, cudaMemsetAsync(mb.hist, 0, sizeof(double) * 3 * std::max(1, history), h->stream));
+    const unsigned char *pf = reinterpret_cast<const unsigned char *>(free_state + 2);  // centre, inertia
+    for (size_t k = 0; k < sizeof(double) * 4; ++k) hh = (hh ^ pf[k]) * 0x100000001b3ULL;
+  }
+  mb.hash = hh;
   mb.on = true;
   ++h->version;
   h->tiles_bx = h->tiles_by = 0;
   h->drop_graphs();
-  // geometry of the pose t0 for the next step (no refill: the state is set afterwards
-  // or was set on the static geometry)
+  // geometry of the first pose for the next step (no refill: the state is set
+  // afterwards or was set on the static geometry)
   cudaError_t err = move_geometry(h, 0, 0, h->f[h->cur], h->cur);
   if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
   if (err != cudaSuccess) return lbm_fail(h, LBM_ERR_CUDA, std::string("moving body: ") + cudaGetErrorString(err));
@@ -997,5 +1162,83 @@ extern "C" int lbm_set_moving_body(lbm_handle h, const lbm_shape *body, const do
   long long nf = 0;
   for (long long n = 0; n < h->np; ++n) nf += (fl[n] & 3) == K_FLUID;
   h->nfluid = nf;
+  return LBM_OK;
+}
+
+static int check_body(lbm_handle h, const lbm_shape *body) {
+  if (!h->geom_ok) return lbm_fail(h, LBM_ERR_STATE, "build the static geometry first");
+  if (h->has_shell) return lbm_fail(h, LBM_ERR_ARG, "a moving body cannot share a geometry with thin shells");
+  if (body->type != LBM_SHAPE_SPHERE && body->type != LBM_SHAPE_ELLIPSOID)
+    return lbm_fail(h, LBM_ERR_ARG, "a moving body is a sphere or an ellipsoid");
+  if (body->tag < 0 || body->tag > 7) return lbm_fail(h, LBM_ERR_ARG, "tags must be 0..7");
+  if (h->bc == LBM_BC_BFL) return lbm_fail(h, LBM_ERR_ARG, "BFL cannot be used with a moving body");
+  return LBM_OK;
+}
+
+extern "C" int lbm_set_moving_body(lbm_handle h, const lbm_shape *body, const double *traj, int ntraj, int t0) {
+  if (!h || !body || !traj) return lbm_fail(h, LBM_ERR_ARG, "null argument");
+  int rc = check_body(h, body);
+  if (rc) return rc;
+  if (ntraj < 2 || t0 < 0) return lbm_fail(h, LBM_ERR_ARG, "the trajectory needs at least two poses");
+  double ext[3];
+  const double rxy = std::max(body->r[0], body->r[1]);
+  for (int a = 0; a < 3; ++a)
+    ext[a] = body->type == LBM_SHAPE_ELLIPSOID ? (a < 2 && body->ang != 0.0 ? rxy : body->r[a]) : body->r[0];
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int k = 0; k < ntraj; ++k)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], traj[9 * k + a]);
+      hi[a] = std::max(hi[a], traj[9 * k + a]);
+    }
+  return setup_body(h, body, lo, hi, ext, traj, ntraj, t0, nullptr, 0);
+}
+
+extern "C" int lbm_set_free_body(lbm_handle h, const lbm_shape *body, double inertia, int history) {
+  if (!h || !body) return lbm_fail(h, LBM_ERR_ARG, "null argument");
+  int rc = check_body(h, body);
+  if (rc) return rc;
+  if (!(inertia > 0.0) || !std::isfinite(inertia)) return lbm_fail(h, LBM_ERR_ARG, "the inertia must be positive");
+  if (history < 0) return lbm_fail(h, LBM_ERR_ARG, "negative history length");
+  // the body turns about z through its centre: it sweeps a disc of its largest
+  // in-plane semi-axis (a sphere: its radius)
+  const double rxy = body->type == LBM_SHAPE_ELLIPSOID ? std::max(body->r[0], body->r[1]) : body->r[0];
+  const double ext[3] = {rxy, rxy, body->type == LBM_SHAPE_ELLIPSOID ? body->r[2] : body->r[0]};
+  const double traj[18] = {body->c[0], body->c[1], body->c[2], 0, 0, 0, 0, 0, 0,
+                           body->c[0], body->c[1], body->c[2], 0, 0, 0, 0, 0, 0};
+  const double state[6] = {body->type == LBM_SHAPE_ELLIPSOID ? body->ang : 0.0, body->om[2],
+                           body->c[0], body->c[1], body->c[2], inertia};
+  return setup_body(h, body, body->c, body->c, ext, traj, 2, 0, state, history);
+}
+
+extern "C" int lbm_get_body_history(lbm_handle h, double *out, int64_t *n) {
+  if (!h || !n) return lbm_fail(h, LBM_ERR_ARG, "null argument");
+  if (!h->mb.on || !h->mb.free_rot) return lbm_fail(h, LBM_ERR_STATE, "no free body");
+  MovingBody &mb = h->mb;
+  int steps = 0;
+  LBM_CUDA_GEO(h, cudaStreamSynchronize(h->stream));
+  LBM_CUDA_GEO(h, cudaMemcpy(&steps, mb.step, sizeof(int), cudaMemcpyDeviceToHost));
+  const long long avail = std::min<long long>(steps, mb.hist_cap);
+  if (!out) { *n = avail; return LBM_OK; }
+  const long long want = std::min<long long>(*n, avail);
+  std::vector<double> all((size_t)3 * std::max(1, mb.hist_cap));
+  LBM_CUDA_GEO(h, cudaMemcpy(all.data(), mb.hist, sizeof(double) * 3 * mb.hist_cap, cudaMemcpyDeviceToHost));
+  // the last `want` entries in step order: step k sits at k % cap
+  for (long long j = 0; j < want; ++j) {
+    const long long k = (steps - want + j) % mb.hist_cap;
+    for (int c = 0; c < 3; ++c) out[3 * j + c] = all[3 * k + c];
+  }
+  *n = want;
+  return LBM_OK;
+}
+
+extern "C" int lbm_set_refill(lbm_handle h, int mode, int iterations) {
+  if (!h) return lbm_fail(nullptr, LBM_ERR_ARG, "null handle");
+  if (mode != LBM_REFILL_EQUILIBRIUM && mode != LBM_REFILL_LIR) return lbm_fail(h, LBM_ERR_ARG, "unknown refill");
+  if (iterations < 0 || iterations > 100000) return lbm_fail(h, LBM_ERR_ARG, "iterations must be 0..100000");
+  h->refill_mode = mode;
+  h->refill_iters = iterations;
+  h->mb.refill_mode = mode;
+  h->mb.refill_iters = iterations;
+  h->drop_graphs();
   return LBM_OK;
 }

@@ -99,11 +99,11 @@ cudaError_t launch_read(int lattice, int dtype, const View &v, const void *fin, 
 
 cudaError_t launch_force(int lattice, int dtype, const View &v, const void *cur, const void *prev,
                          const RecSet &rs, long long nrec, const int *nrec_dev, int tag, double *part,
-                         const Launch &l) {
+                         const Launch &l, double *tpart, double cx, double cy, double cz) {
   return dispatch(lattice, dtype, [&]<class L, typename S, typename M>() {
     k_force<L, S, M><<<l.grid, l.block, 0, l.stream>>>(v, static_cast<const S *>(cur),
                                                        static_cast<const S *>(prev), rs, nrec,
-                                                       nrec_dev, tag, part);
+                                                       nrec_dev, tag, part, tpart, cx, cy, cz);
     return cudaGetLastError();
   });
 }

@@ -546,6 +546,16 @@ __device__ __forceinline__ void boundary_node(const View &v, const RecSet &rs, c
   boundary<L, S, M>(v, rs, r, fs, stride, m, pi, n, x, y, z, fout);
 }
 
+// Column and row of lattice tile t in its plane, t / gx by one wide multiply and
+// a shift (division by an invariant integer, Granlund and Montgomery): with
+// l = floor(log2 gx), gx_m = ceil(2^(32+l) / gx) < 2^32 and gx_s = 32 + l, or
+// gx_m = 2^31 and gx_s = 31 + l when gx is a power of two. The error of the
+// product is below t / 2^(32+l) < 1 / (2 gx) for t < 2^31, so the quotient is exact.
+__device__ __forceinline__ int2 tile_coords(const View &v, int t) {
+  const int ty = (int)(((unsigned long long)(unsigned)t * v.gx_m) >> v.gx_s);
+  return make_int2(t - ty * v.gx, ty);
+}
+
 // ---------------------------------------------------------------- the fused step
 // One launch does the whole update t -> t+1. Each block takes one entry of the
 // tile table v.tiles:
@@ -575,8 +585,9 @@ __device__ __forceinline__ void boundary_node(const View &v, const RecSet &rs, c
 template <class L, typename S, typename M, int PHYS>
 __device__ __forceinline__ void lattice_tile(const View &v, const S *__restrict__ fin,
                                              S *__restrict__ fout, int2 tile) {
-  const int x = (tile.y % v.gx) * blockDim.x + threadIdx.x;
-  const int y = (tile.y / v.gx) * blockDim.y + threadIdx.y;
+  const int2 tc = tile_coords(v, tile.y);
+  const int x = tc.x * blockDim.x + threadIdx.x;
+  const int y = tc.y * blockDim.y + threadIdx.y;
   const int z = tile.x;
   if (y >= v.ny) return;  // uniform across the warp
   const int n = (z * v.ny + y) * v.nxp + x;
@@ -660,8 +671,9 @@ __device__ __forceinline__ void lattice_tile_pair(const View &v, const S *__rest
   using V = Vec2<S>;
   using T = typename V::T;
   const int lane = threadIdx.x & 31;
-  const int x = (tile.y % v.gx) * (2 * blockDim.x) + 2 * threadIdx.x;
-  const int y = (tile.y / v.gx) * blockDim.y + threadIdx.y;
+  const int2 tc = tile_coords(v, tile.y);
+  const int x = tc.x * (2 * blockDim.x) + 2 * threadIdx.x;
+  const int y = tc.y * blockDim.y + threadIdx.y;
   const int z = tile.x;
   if (y >= v.ny) return;  // uniform across the warp
   const int n = (z * v.ny + y) * v.nxp + x;
@@ -887,7 +899,8 @@ __device__ void tma_issue(const View &v, const S *__restrict__ fin, int2 tile, u
                           uint64_t *bar, const TmaLayout<S> &lay, int lane) {
   constexpr int HALO = TmaLayout<S>::HALO;
   const int W = lay.W, H = lay.H;
-  const int z = tile.x, x0 = (tile.y % v.gx) * W, y0 = (tile.y / v.gx) * H;
+  const int2 tc = tile_coords(v, tile.y);
+  const int z = tile.x, x0 = tc.x * W, y0 = tc.y * H;
   const int xa = max(x0 - HALO, 0), xb = min(x0 + W + HALO, v.nxp);
   const int rows = min(H, v.ny - y0);
   const uint32_t rowbytes = (uint32_t)((xb - xa) * (int)sizeof(S));
@@ -919,8 +932,9 @@ __device__ __forceinline__ void tma_lattice(const View &v, const S *__restrict__
                                             int2 tile, const unsigned char *base, const TmaLayout<S> &lay) {
   constexpr int HALO = TmaLayout<S>::HALO;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int x = (tile.y % v.gx) * lay.W + tx;
-  const int y = (tile.y / v.gx) * lay.H + ty;
+  const int2 tc = tile_coords(v, tile.y);
+  const int x = tc.x * lay.W + tx;
+  const int y = tc.y * lay.H + ty;
   const int z = tile.x;
   if (y >= v.ny) return;  // uniform across the warp
   const int n = (z * v.ny + y) * v.nxp + x;
@@ -1193,14 +1207,18 @@ __global__ void __launch_bounds__(256) k_read(const View v, const S *__restrict_
 // Links on the inner side of a thin shell (tag TAG_INNER) carry no force. On its
 // outer side the node's own slot ibar holds the value written ahead from the
 // other side, so f*_ibar(x_F, t) is computed again from the state at t, prev.
+// With tpart non-null the kernel also writes the per-block partial of the torque
+// about (cx, cy, cz), sum (x_W - c) x F_link with x_W = x_F - q c_i the link's wall
+// point (3 doubles).
 template <class L, typename S, typename M>
 __global__ void __launch_bounds__(256) k_force(const View v, const S *__restrict__ cur,
                                                const S *__restrict__ prev, RecSet rs,
                                                long long nrec, const int *nrec_dev, int tag,
-                                               double *__restrict__ part) {
+                                               double *__restrict__ part, double *__restrict__ tpart,
+                                               double cx, double cy, double cz) {
   const long long rid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (nrec_dev) nrec = *nrec_dev;
-  double fx = 0.0, fy = 0.0, fz = 0.0;
+  double fx = 0.0, fy = 0.0, fz = 0.0, tx = 0.0, ty = 0.0, tz = 0.0;
   if (rid < nrec) {
     const Rec r = rs.rec[rid];
     const long long n = rs.rnode[rid];
@@ -1241,24 +1259,42 @@ __global__ void __launch_bounds__(256) k_force(const View v, const S *__restrict
       fnew += w * v.rho0;
       double wx = 0.0, wy = 0.0, wz = 0.0;
       if (luw) { wx = (double)luw[3 * li]; wy = (double)luw[3 * li + 1]; wz = (double)luw[3 * li + 2]; }
-      fx += (-L::cx(i) - wx) * fpost_ib - (L::cx(i) - wx) * fnew;
-      fy += (-L::cy(i) - wy) * fpost_ib - (L::cy(i) - wy) * fnew;
-      fz += (-L::cz(i) - wz) * fpost_ib - (L::cz(i) - wz) * fnew;
+      const double gx = (-L::cx(i) - wx) * fpost_ib - (L::cx(i) - wx) * fnew;
+      const double gy = (-L::cy(i) - wy) * fpost_ib - (L::cy(i) - wy) * fnew;
+      const double gz = (-L::cz(i) - wz) * fpost_ib - (L::cz(i) - wz) * fnew;
+      fx += gx;
+      fy += gy;
+      fz += gz;
+      if (tpart) {
+        const double q = (double)lq[li];
+        const double rx = x - q * L::cx(i) - cx, ry = y - q * L::cy(i) - cy,
+                     rz = L::D == 3 ? z - q * L::cz(i) - cz : 0.0;
+        tx += ry * gz - rz * gy;
+        ty += rz * gx - rx * gz;
+        tz += rx * gy - ry * gx;
+      }
     }
   }
-  __shared__ double sm[3][8];
+  __shared__ double sm[6][8];
   for (int o = 16; o > 0; o >>= 1) {
     fx += __shfl_down_sync(0xffffffffu, fx, o);
     fy += __shfl_down_sync(0xffffffffu, fy, o);
     fz += __shfl_down_sync(0xffffffffu, fz, o);
+    tx += __shfl_down_sync(0xffffffffu, tx, o);
+    ty += __shfl_down_sync(0xffffffffu, ty, o);
+    tz += __shfl_down_sync(0xffffffffu, tz, o);
   }
   const int t = threadIdx.x;
-  if ((t & 31) == 0) { sm[0][t >> 5] = fx; sm[1][t >> 5] = fy; sm[2][t >> 5] = fz; }
+  if ((t & 31) == 0) {
+    sm[0][t >> 5] = fx; sm[1][t >> 5] = fy; sm[2][t >> 5] = fz;
+    sm[3][t >> 5] = tx; sm[4][t >> 5] = ty; sm[5][t >> 5] = tz;
+  }
   __syncthreads();
-  if (t < 3) {
+  if (t < 6) {
     double s = 0.0;
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sm[t][k];
-    part[(long long)blockIdx.x * 3 + t] = s;
+    if (t < 3) part[(long long)blockIdx.x * 3 + t] = s;
+    else if (tpart) tpart[(long long)blockIdx.x * 3 + t - 3] = s;
   }
 }
 

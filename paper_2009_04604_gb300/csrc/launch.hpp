@@ -38,9 +38,12 @@ cudaError_t launch_read(int lattice, int dtype, const View &v, const void *fin, 
 // (device) when nrec_dev is not null; the grid must cover the largest count.
 // cur is the state the last step wrote, prev the state it read (used for the
 // links across thin shells; may be null when rs has none).
+// With tpart, also the torque about (cx, cy, cz) of every link force, taken at the
+// link's wall point x_F - q c_i (3 doubles per block).
 cudaError_t launch_force(int lattice, int dtype, const View &v, const void *cur, const void *prev,
                          const RecSet &rs, long long nrec, const int *nrec_dev, int tag, double *part,
-                         const Launch &l);
+                         const Launch &l, double *tpart = nullptr, double cx = 0.0, double cy = 0.0,
+                         double cz = 0.0);
 // amask[n] of every padded node (View::amask) from the node kinds in v.flags
 // (geometry.cu).
 cudaError_t launch_amask(int lattice, const View &v, uint32_t *amask, cudaStream_t s);

@@ -289,6 +289,13 @@ View lbm_sim::view() const {
   v.err = err_dev;
   v.wait_limit = wait_limit;
   v.tiles = tiles; v.gx = nxp / (step_bx * npt());
+  {  // multiplier and shift of t / gx (tile_coords): l = floor(log2 gx)
+    const unsigned d = (unsigned)(v.gx > 0 ? v.gx : 1);
+    unsigned l = 0;
+    while ((2ull << l) <= d) ++l;
+    if ((d & (d - 1)) == 0) { v.gx_m = 1u << 31; v.gx_s = 31 + l; }
+    else { v.gx_m = (uint32_t)(((1ull << (32 + l)) + d - 1) / d); v.gx_s = 32 + l; }
+  }
   for (int i = 0; i < Q; ++i) {
     int c[3];
     lattice_c(i, c[0], c[1], c[2]);
@@ -488,6 +495,29 @@ extern "C" int lbm_wall_force(lbm_handle h, int tag, double F[3]) {
   }
   LBM_CUDA(h, launch_reduce_final(h->scratch, nblk1 + nblk2, 3, h->dres, h->stream));
   LBM_CUDA(h, cudaMemcpyAsync(F, h->dres, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+extern "C" int lbm_wall_torque(lbm_handle h, int tag, const double centre[3], double T[3]) {
+  if (!h || !T || !centre) return lbm_fail(h, LBM_ERR_ARG, "null argument");
+  if (!h->geom_ok || !h->state_ok) return lbm_fail(h, LBM_ERR_STATE, "no state yet");
+  if (tag < -1 || tag > 7) return lbm_fail(h, LBM_ERR_ARG, "tag must be -1..7");
+  T[0] = T[1] = T[2] = 0.0;
+  const int bs = 256;
+  const long long nblk = (h->nb + bs - 1) / bs;
+  if (nblk == 0) return LBM_OK;
+  int rc = h->ensure_scratch(nblk * 6);
+  if (rc) return rc;
+  Launch l;
+  l.block = dim3(bs);
+  l.grid = dim3((unsigned)nblk);
+  l.stream = h->stream;
+  const View v = h->view();
+  LBM_CUDA(h, launch_force(h->lattice, h->dtype, v, h->f[h->cur], h->f[h->cur ^ 1], v.stat(), h->nb, nullptr, tag,
+                           h->scratch, l, h->scratch + nblk * 3, centre[0], centre[1], centre[2]));
+  LBM_CUDA(h, launch_reduce_final(h->scratch + nblk * 3, nblk, 3, h->dres, h->stream));
+  LBM_CUDA(h, cudaMemcpyAsync(T, h->dres, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   LBM_CUDA(h, cudaStreamSynchronize(h->stream));
   return LBM_OK;
 }
@@ -746,6 +776,7 @@ struct SaveHeader {
   double rho0;
   uint64_t geom_hash, body_hash;
   int64_t pose;  // the moving body's pose index, -1 without a body
+  double body_state[6];  // free body: angle, omega, centre, inertia
   uint64_t pop_bytes;
 };
 constexpr uint32_t kSaveVersion = 1;
@@ -774,6 +805,7 @@ extern "C" int lbm_save(lbm_handle h, void *buf, size_t *bytes) {
     int k = 0;
     LBM_CUDA(h, cudaMemcpy(&k, h->mb.step, sizeof(int), cudaMemcpyDeviceToHost));
     hd.pose = k;
+    if (h->mb.free_rot) LBM_CUDA(h, cudaMemcpy(hd.body_state, h->mb.state, sizeof(hd.body_state), cudaMemcpyDeviceToHost));
   }
   unsigned char *p = static_cast<unsigned char *>(buf);
   std::memcpy(p, &hd, sizeof(hd));
@@ -805,6 +837,8 @@ extern "C" int lbm_load(lbm_handle h, const void *buf, size_t bytes) {
   LBM_CUDA(h, cudaMemcpyAsync(h->f[h->cur], p + sizeof(hd), pop, cudaMemcpyHostToDevice, h->stream));
   LBM_CUDA(h, cudaStreamSynchronize(h->stream));
   if (h->mb.on) {
+    if (h->mb.free_rot)
+      LBM_CUDA(h, cudaMemcpy(h->mb.state, hd.body_state, sizeof(hd.body_state), cudaMemcpyHostToDevice));
     int rc = h->move_rebuild(hd.pose);
     if (rc) return rc;
   }

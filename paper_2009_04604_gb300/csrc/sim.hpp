@@ -35,6 +35,15 @@ struct MovingBody {
   double *fpart = nullptr;         // device: per-block momentum-exchange partials of the last step
   long long nfpart = 0;            // blocks
   unsigned long long hash = 0;     // FNV-1a of the body's shape and trajectory table
+  // free rotation about a fixed axis through the body's centre, driven by the fluid torque
+  bool free_rot = false;
+  double *state = nullptr;         // device [angle, omega, c0, c1, c2, inertia]
+  double centre[3] = {0.0, 0.0, 0.0};
+  double *tpart = nullptr;         // device: per-block torque partials (about centre) of the last step
+  double *hist = nullptr;          // device [hist_cap][3]: angle, omega, torque after each step
+  int hist_cap = 0;
+  int refill_mode = 0, refill_iters = 10;  // lbm_refill of fresh nodes, LIR iterations
+  uint8_t *nkind = nullptr;        // device [rpad]: the region's kinds at the new pose (LIR)
 };
 
 struct lbm_sim {
@@ -74,6 +83,7 @@ struct lbm_sim {
   long long scratch_len = 0;
   double *stage_f = nullptr;  // FP64 staging of lbm_set/get_populations (N*Q, device; kept)
   long long wait_limit = 1LL << 24;  // first-wait poll limit of the TMA-staged step
+  int refill_mode = 0, refill_iters = 10;  // lbm_set_refill, kept for bodies set later
 
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // captured step loops, by starting buffer
   int2 *tiles = nullptr;      // step-kernel tile table (device)

@@ -24,6 +24,7 @@ BC_ELIBB_F, BC_ELIBB_FQ, BC_BFL, BC_HWBB, BC_ELIBB_U, BC_ELIBB_UQ = 0, 1, 2, 3, 
 COLL_BGK, COLL_TRT = 0, 1
 NEQ_BOUNCE_BACK, NEQ_REGULARIZED = 0, 1
 FLUID, SOLID, OPEN = 0, 1, 2
+REFILL_EQUILIBRIUM, REFILL_LIR = 0, 1
 SHAPE_TYPES = {"sphere": 0, "sphere_out": 1, "ellipsoid": 2, "strip": 3, "shell": 4}
 DTYPES = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
 BCS = {"elibb_f": BC_ELIBB_F, "elibb_fq": BC_ELIBB_FQ, "bfl": BC_BFL, "hwbb": BC_HWBB,
@@ -45,7 +46,8 @@ class Shape(ctypes.Structure):
                 ("nrm", ctypes.c_double * 3), ("off", ctypes.c_double),
                 ("width", ctypes.c_double), ("period", ctypes.c_double),
                 ("v", ctypes.c_double * 3), ("om", ctypes.c_double * 3),
-                ("v1", ctypes.c_double * 3), ("om1", ctypes.c_double * 3)]
+                ("v1", ctypes.c_double * 3), ("om1", ctypes.c_double * 3),
+                ("ang", ctypes.c_double)]
 
 
 _lib = None
@@ -79,6 +81,10 @@ _SIGS = {
     "lbm_load": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
     "lbm_set_wait_limit": [ctypes.c_void_p, ctypes.c_longlong],
     "lbm_set_moving_body": [ctypes.c_void_p, P(Shape), _d, ctypes.c_int, ctypes.c_int],
+    "lbm_set_free_body": [ctypes.c_void_p, P(Shape), ctypes.c_double, ctypes.c_int],
+    "lbm_get_body_history": [ctypes.c_void_p, _d, _i64],
+    "lbm_wall_torque": [ctypes.c_void_p, ctypes.c_int, _d, _d],
+    "lbm_set_refill": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int],
     "lbm_batch_create": [P(ctypes.c_void_p), ctypes.c_int, P(ctypes.c_void_p)],
     "lbm_batch_destroy": [ctypes.c_void_p],
     "lbm_batch_step": [ctypes.c_void_p, ctypes.c_int],
@@ -231,6 +237,31 @@ class Simulation:
         traj = _f64(traj, (-1, 9))
         arr = make_shapes([body])
         self._ok(self.lib.lbm_set_moving_body(self.h, arr, _np_ptr(traj, ctypes.c_double), traj.shape[0], int(t0)))
+
+    def set_free_body(self, body, inertia, history=0):
+        """Rigid body (dict spec: sphere or ellipsoid, with c, r, ang, om) turning freely
+        about z through its centre under the fluid torque (lbm_set_free_body)."""
+        arr = make_shapes([body])
+        self._ok(self.lib.lbm_set_free_body(self.h, arr, float(inertia), int(history)))
+
+    def set_refill(self, mode="equilibrium", iterations=10):
+        """Refill of fresh nodes: "equilibrium" or "lir" (local iteration refill)."""
+        m = {"equilibrium": REFILL_EQUILIBRIUM, "lir": REFILL_LIR}[mode] if isinstance(mode, str) else int(mode)
+        self._ok(self.lib.lbm_set_refill(self.h, m, int(iterations)))
+
+    def body_history(self):
+        """[steps, 3] array: angle, angular velocity after each step and the step's torque."""
+        n = ctypes.c_int64(0)
+        self._ok(self.lib.lbm_get_body_history(self.h, None, ctypes.byref(n)))
+        out = np.zeros((max(n.value, 1), 3))
+        self._ok(self.lib.lbm_get_body_history(self.h, _np_ptr(out, ctypes.c_double), ctypes.byref(n)))
+        return out[:n.value]
+
+    def wall_torque(self, centre, tag=-1):
+        c = np.ascontiguousarray(centre, dtype=np.float64)
+        T = np.zeros(3)
+        self._ok(self.lib.lbm_wall_torque(self.h, int(tag), _np_ptr(c, ctypes.c_double), _np_ptr(T, ctypes.c_double)))
+        return T
 
     def init(self, rho=1.0, u=(0.0, 0.0, 0.0)):
         U = (ctypes.c_double * 3)(*[float(x) for x in u])

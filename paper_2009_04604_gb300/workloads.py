@@ -6,7 +6,8 @@ the base node kinds (walls, inlet, outlet), the base wall velocities and a list
 of analytic shapes. Shapes are dicts with string types
 ('sphere', 'sphere_out', 'ellipsoid', 'strip'). The inputs follow the
 workloads the paper tests on (Sec. III) and the benchmark configurations:
-an inclined channel, circular Couette, a sphere in a duct, a periodic porous
+an inclined channel, circular Couette, a shear channel with an elliptic
+cylinder, a sphere in a duct, a periodic porous
 medium with a moving sphere, and batches of ducts.
 """
 from __future__ import annotations
@@ -51,6 +52,29 @@ def circular_couette(L, tau=0.8, u_inner=0.01, centre=None):
     return dict(lattice=D2Q9, dims=(L, L, 1), tau=tau, xshift=0, force=(0.0, 0.0, 0.0),
                 base=None, base_u=None, shapes=shapes, rho0=1.0, R1=R1, R2=R2, centre=(cx, cy),
                 omega1=om)
+
+
+def shear_channel_ellipse(nx=128, ny=98, U=0.04, tau=0.8, ra=8.0, rb=4.0, ang0=0.0):
+    """D2Q9 shear channel for Jeffery's orbit (Sec. III.C): walls at rows 0 and
+    ny-1 moving at -U/2 and +U/2 (half-way walls, so the channel height is
+    H = ny - 2), the linear shear flow u_x = -U/2 + U (y - 1/2) / H as the initial
+    state, and an elliptic cylinder at the centre with semi-axes rb along its body
+    x axis and ra along its body y axis (vertical at ang0 = 0). Its moment of
+    inertia is the solid ellipse's at density 1, pi ra rb (ra^2 + rb^2) / 4."""
+    H = ny - 2
+    y = np.arange(nx * ny) // nx
+    base = np.zeros(nx * ny, np.uint8)
+    base[(y == 0) | (y == ny - 1)] = SOLID
+    base_u = np.zeros((nx * ny, 3))
+    base_u[y == 0, 0] = -0.5 * U
+    base_u[y == ny - 1, 0] = 0.5 * U
+    u0 = np.zeros((nx * ny, 3))
+    u0[:, 0] = -0.5 * U + U * (y - 0.5) / H
+    centre = (nx / 2.0 - 0.3, (ny - 1) / 2.0, 0.0)
+    body = dict(type="ellipsoid", tag=1, c=centre, r=(rb, ra, 1.0), ang=ang0)
+    return dict(lattice=D2Q9, dims=(nx, ny, 1), tau=tau, xshift=0, force=(0.0, 0.0, 0.0), rho0=1.0,
+                base=base, base_u=base_u, shapes=[], u0=u0, body=body,
+                inertia=math.pi * ra * rb * (ra * ra + rb * rb) / 4.0, gamma=U / H, U=U, aspect=ra / rb)
 
 
 def duct_base(dims, u_in):

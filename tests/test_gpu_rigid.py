@@ -1,0 +1,162 @@
+"""Rigid-body coupling (Sec. III.C, Jeffery's orbit; App. D torque fluctuation).
+
+An elliptic cylinder (D2Q9) sits at the centre of a channel whose walls move at
+-U/2 and +U/2; the fluid starts from the linear shear profile. The body turns
+freely about its centre under the momentum-exchange torque (lbm_set_free_body):
+omega += T / I, angle += omega after each step, with its link geometry rebuilt at
+the new angle on the device and uncovered nodes refilled.
+
+1. FP64 parity with the oracle stepping the same coupling on the host (its own
+   torque reduction, oracle.torque, its own geometry at each angle, and its own
+   refill of uncovered nodes, by equilibrium or by local iterations): the angle,
+   angular velocity and torque of every step, and the populations.
+2. The static torque reduction (lbm_wall_torque) against oracle.torque.
+3. Jeffery's orbit over 1.2 quarter turns against the oracle's run of the same
+   coupling (tests/golden/jeffery_ellipse_128x98.npz), the closed form
+   (oracle.analytic.jeffery_angle, aspect ratio r_a / r_b) at the qualitative
+   level the paper reports, and the torque squared fluctuation (App. D,
+   Eq. TSF30) against the oracle's BFL runs."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import analytic as A
+from paper_2009_04604_gb300 import build, lbm
+from paper_2009_04604_gb300 import workloads as W
+
+from gpu_helpers import perm, rel_l2, to_lib, to_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    oracle.build()
+    lbm.load()
+
+
+def _channel(nx=96, ny=66, U=0.02, ang0=0.0):
+    return W.shear_channel_ellipse(nx=nx, ny=ny, U=U, tau=0.8, ra=8.0, rb=4.0, ang0=ang0)
+
+
+def _oracle_run(ch, steps, bc=oracle.BC_ELIBB_F, lir=0):
+    p = oracle.params(oracle.D2Q9, ch["dims"], ch["tau"], bc=bc)
+    body = dict(ch["body"], type=oracle.SHAPE_ELLIPSOID)
+    flags, *_ = oracle.geometry(p, ch["base"], ch["base_u"], [body])
+    f0 = oracle.init_eq(p, flags, None, ch["u0"])
+    flags, f, hist = oracle.free_rotation(p, ch["base"], ch["base_u"], body, ch["inertia"], f0, steps, lir=lir)
+    return p, f0, f, flags, hist
+
+
+def _gpu(ch, f0, dtype=lbm.F64, history=100000, bc=lbm.BC_ELIBB_F, lir=0):
+    s = lbm.Simulation(lbm.D2Q9, ch["dims"], ch["tau"], dtype)
+    s.set_options(bc, 1.0, (0, 0, 0), 0)
+    if lir:
+        s.set_refill("lir", lir)
+    s.build_geometry(ch["base"], ch["base_u"], [])
+    s.set_free_body(ch["body"], ch["inertia"], history)
+    s.set_populations(to_lib(f0, perm(lbm.D2Q9)))
+    return s
+
+
+@pytest.mark.parametrize("lir", [0, 12])
+def test_free_rotation_matches_oracle_fp64(lir):
+    """Free rotation with the equilibrium refill (lir = 0) and the local iteration
+    refill (12 iterations) of uncovered nodes."""
+    ch = _channel(ang0=0.35)
+    steps = 120
+    p, f0, f, flags, hist = _oracle_run(ch, steps, lir=lir)
+    s = _gpu(ch, f0, lir=lir)
+    s.step(steps)
+    gh = s.body_history()
+    assert gh.shape == (steps, 3)
+    assert np.abs(gh[:, 0] - hist[:, 0]).max() < 1e-12 * max(1.0, np.abs(hist[:, 0]).max())
+    assert np.abs(gh[:, 1] - hist[:, 1]).max() < 1e-10 * np.abs(hist[:, 1]).max()
+    assert np.abs(gh[:, 2] - hist[:, 2]).max() < 1e-10 * np.abs(hist[:, 2]).max()
+    assert np.array_equal(s.get_geometry()[0], flags)
+    g = to_oracle(s.get_populations(), perm(lbm.D2Q9))
+    fl = flags == 0
+    assert rel_l2(g[fl], f[fl]) < 1e-12
+    s.close()
+
+
+def test_wall_torque_matches_oracle():
+    """Static geometry: lbm_wall_torque (FP64) equals oracle.torque of the same step."""
+    ch = _channel(ang0=0.7)
+    p = oracle.params(oracle.D2Q9, ch["dims"], ch["tau"], bc=oracle.BC_ELIBB_FQ)
+    shape = dict(ch["body"], type=oracle.SHAPE_ELLIPSOID, om=(0, 0, -2e-4), om1=(0, 0, -2e-4))
+    flags, q, uw, uw1, tag = oracle.geometry(p, ch["base"], ch["base_u"], [shape])
+    f = oracle.init_eq(p, flags, None, ch["u0"])
+    s = lbm.Simulation(lbm.D2Q9, ch["dims"], ch["tau"], lbm.F64)
+    s.set_options(lbm.BC_ELIBB_FQ, 1.0, (0, 0, 0), 0)
+    s.build_geometry(ch["base"], ch["base_u"], [dict(ch["body"], om=(0, 0, -2e-4), om1=(0, 0, -2e-4))])
+    s.set_populations(to_lib(f, perm(lbm.D2Q9)))
+    for _ in range(9):
+        f, flink = oracle.step(p, flags, f, q, uw, uw1, want_force=True)
+    s.step(9)
+    c = ch["body"]["c"]
+    for tg in (-1, 0, 1):
+        ref = oracle.torque(p, q, tag, flink, c, tg)
+        got = s.wall_torque(c, tg)
+        assert np.abs(got - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max()), (tg, got, ref)
+    s.close()
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "jeffery_ellipse_128x98.npz")
+
+
+@pytest.mark.parametrize("lir", [0, 12])
+def test_jeffery_orbit_and_torque_fluctuation(lir):
+    """Free ellipse (aspect ratio 2) in shear over 1.2 quarter turns of the
+    closed-form orbit, ELIBB-F with the equilibrium refill (lir = 0) or the local
+    iteration refill (12 iterations), against the oracle's run of the same
+    coupling (tests/golden/make_jeffery_reference.py): the angle every 10 steps,
+    the step of the quarter turn, and the mean torque squared fluctuation (App. D,
+    Eq. TSF30) from step 500 to the quarter turn. Then Jeffery's closed form at the
+    qualitative level of the paper's figures, and the paper's reading of the
+    fluctuation: without a refill scheme the local rule fluctuates more than BFL
+    (the oracle's BFL run of the same case), with the local iteration refill it
+    comes close to it."""
+    ref = np.load(GOLDEN)
+    nx, ny, U, tau, ra, rb = ref["channel"]
+    ch = W.shear_channel_ellipse(nx=int(nx), ny=int(ny), U=U, tau=tau, ra=ra, rb=rb)
+    p = oracle.params(oracle.D2Q9, ch["dims"], ch["tau"])
+    flags, *_ = oracle.geometry(p, ch["base"], ch["base_u"], [dict(ch["body"], type=oracle.SHAPE_ELLIPSOID)])
+    f0 = oracle.init_eq(p, flags, None, ch["u0"])
+    steps = int(ref["steps"])
+    s = _gpu(ch, f0, history=steps, lir=lir)
+    s.step(steps)
+    h = s.body_history()
+    s.close()
+    key = f"elibb_f_lir{lir}"
+    every, t0 = int(ref["every"]), int(ref["t_start"])
+    theta = -h[:, 0]
+    k = int(np.searchsorted(theta, math.pi / 2))
+    t = np.arange(1, steps + 1, dtype=float)
+    _, tsf, _ = A.torque_squared_fluctuation(t[t0:k], h[t0:k, 2])
+    tsf = float(tsf.mean())
+    print(f"{key}: quarter turn at {k} (oracle {int(ref[key + '_quarter'])}), mean TSF {tsf:.4e} "
+          f"(oracle {float(ref[key + '_tsf']):.4e}), oracle BFL {float(ref[f'bfl_lir{lir}_tsf']):.4e}")
+    # parity with the oracle's coupling
+    assert np.abs(h[every - 1::every, 0] - ref[key + "_angle"]).max() < 1e-6
+    assert abs(k - int(ref[key + "_quarter"])) <= 1
+    assert abs(tsf - float(ref[key + "_tsf"])) <= 0.02 * float(ref[key + "_tsf"])
+    # Jeffery's closed form (aspect ratio r_a / r_b), at the qualitative level of the paper
+    gam, aspect = ch["gamma"], ch["aspect"]
+    t_quarter = (math.pi / 2) * (aspect * aspect + 1) / (gam * aspect)
+    assert abs(k - t_quarter) / t_quarter < 0.15
+    assert np.abs(theta - A.jeffery_angle(t, gam, aspect)).max() < 0.25
+    # the fluctuation against the non-local rule
+    bfl = float(ref[f"bfl_lir{lir}_tsf"])
+    if lir == 0:
+        assert tsf > 2.0 * bfl
+    else:
+        assert tsf < 1.5 * bfl
+        assert tsf < 0.7 * float(ref["elibb_f_lir0_tsf"])

@@ -219,3 +219,54 @@ def test_lir_iteration_start_and_fixed_point(oracle_lib):
         for i in unknown:
             target = post[opp[i]] + 2 * w[i] * rho * (c[i] @ ub[n]) * 3.0
             assert abs(fn[i] - target) < 1e-13, (n, i, fn[i], target)
+
+
+def test_free_cylinder_spins_at_half_the_shear_rate(oracle_lib):
+    """A free circular cylinder at the centre of a shear channel turns at the
+    fluid's own rotation rate, half its vorticity: omega = -gamma/2 for
+    u_x = gamma y. This pins free_rotation as a whole, in its sign and its size:
+    the torque of the link forces about the centre, the wall velocity
+    omega x (x_W - c) of the rotating wall and the Euler update of omega. A
+    circle covers the same nodes at every angle, so no refill takes part. The
+    spin-up time I / (4 pi mu R^2) is about 11 steps; at 200 steps the rate is
+    within 1% of -gamma/2 (the walls, 14 radii apart here, shift it by a few
+    parts in a thousand)."""
+    from paper_2009_04604_gb300 import workloads as W
+    R = 3.0
+    ch = W.shear_channel_ellipse(nx=48, ny=34, U=0.02, tau=0.8, ra=R, rb=R)
+    body = dict(ch["body"], type=oracle.SHAPE_SPHERE, r=(R, 0.0, 0.0))
+    p = oracle.params(oracle.D2Q9, ch["dims"], ch["tau"])
+    flags, *_ = oracle.geometry(p, ch["base"], ch["base_u"], [body])
+    f0 = oracle.init_eq(p, flags, None, ch["u0"])
+    inertia = np.pi * R ** 4 / 2.0       # solid disc of density 1
+    _, _, h = oracle.free_rotation(p, ch["base"], ch["base_u"], body, inertia, f0, 200)
+    ratio = h[-1, 1] / (-0.5 * ch["gamma"])
+    assert abs(ratio - 1.0) < 0.01, ratio
+    # the angle is the running sum of the rates
+    assert np.allclose(np.cumsum(h[:, 1]), h[:, 0], rtol=0, atol=1e-15)
+
+
+def test_jeffery_reference_follows_the_closed_form():
+    """The oracle's Jeffery runs stored in tests/golden/jeffery_ellipse_128x98.npz
+    (written by make_jeffery_reference.py from oracle.free_rotation) against what
+    the paper fixes: the angle follows Jeffery's closed form for the aspect ratio
+    r_a / r_b = 2 (Sec. III.C; the quarter turn within 8 % and the angle within
+    0.1 rad), and the torque squared fluctuation (App. D) orders as the paper
+    reports: without a refill scheme the local rule ELIBB-F fluctuates well above
+    BFL, with the local iteration refill it drops and comes close to BFL."""
+    import math
+    import os
+    ref = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "jeffery_ellipse_128x98.npz"))
+    nx, ny, U, tau, ra, rb = ref["channel"]
+    gam, aspect = U / (ny - 2), ra / rb
+    every = int(ref["every"])
+    t_quarter = (math.pi / 2) * (aspect * aspect + 1) / (gam * aspect)
+    for key in ("elibb_f_lir0", "elibb_f_lir12", "bfl_lir0", "bfl_lir12"):
+        theta = -ref[key + "_angle"]
+        t = every * np.arange(1, theta.size + 1, dtype=float)
+        assert np.abs(theta - A.jeffery_angle(t, gam, aspect)).max() < 0.1, key
+        assert abs(int(ref[key + "_quarter"]) - t_quarter) < 0.08 * t_quarter, key
+    tsf = {k: float(ref[k + "_tsf"]) for k in ("elibb_f_lir0", "elibb_f_lir12", "bfl_lir0", "bfl_lir12")}
+    assert tsf["elibb_f_lir0"] > 2.0 * tsf["bfl_lir0"]
+    assert tsf["elibb_f_lir12"] < 0.7 * tsf["elibb_f_lir0"]
+    assert tsf["elibb_f_lir12"] < 1.5 * tsf["bfl_lir12"]
