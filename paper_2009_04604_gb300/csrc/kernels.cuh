@@ -97,14 +97,18 @@ __device__ __forceinline__ bool fills_sector(uint8_t fl, uint32_t fluid_bal, int
 // multiply-add, in the order written). The moments, the relaxation and the
 // boundary rule are written with them: the compiler is then free neither to fuse
 // nor to split an operation, so every kernel that inlines them (the step
-// variants, the batched step, the TMA-staged step) rounds exactly alike.
+// variants, the batched step, the TMA-staged step) rounds exactly alike. The
+// FP32 division is the hardware reciprocal times the dividend (__fdividef: at
+// most 2 ulp from the rounded quotient for divisors of normal magnitude, which
+// 1/rho and the boundary rule's q, 1-q and 2q^2 are), deterministic like the
+// rest; FP64 divides with correct rounding.
 template <typename M> struct Ex;
 template <> struct Ex<float> {
   static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
   static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
   static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
   static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
 };
 template <> struct Ex<double> {
   static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
@@ -324,13 +328,13 @@ __device__ __forceinline__ M feq_r(int i, M drho, M rho, M ux, M uy, M uz, M usq
 
 // post-collision value (with the Guo source) of direction i, whose opposite
 // population is fo, for a run-time direction; BGK or TRT as in relax
-template <class L, typename M>
+template <class L, typename M, bool BGK = false>
 __device__ __forceinline__ M post_r(const View &v, const Par<M> &P, int i, M fi, M fo, const Macro<L, M> &m) {
   using X = Ex<M>;
   const M w = dweight<L, M>(i);
   const M cu = cdot_r<L, M>(i, m.ux, m.uy, m.uz);
   M r;
-  if (v.trt) {
+  if (!BGK && v.trt) {
     const M e2 = X::fma(X::mul(M(4.5), cu), cu, X::mul(M(-1.5), m.usq));
     const M ep = X::mul(w, X::fma(m.rho, e2, m.drho));
     const M em = X::mul(X::mul(M(3), w), X::mul(m.rho, cu));
@@ -343,7 +347,7 @@ __device__ __forceinline__ M post_r(const View &v, const Par<M> &P, int i, M fi,
     const M cF = cdot_r<L, M>(i, P.F[0], P.F[1], P.F[2]);
     const M uF = X::fma(m.uz, P.F[2], X::fma(m.uy, P.F[1], X::mul(m.ux, P.F[0])));
     const M kp = X::fma(M(-0.5), P.omega, M(1));
-    const M km = X::fma(M(-0.5), v.trt ? P.omega_m : P.omega, M(1));
+    const M km = X::fma(M(-0.5), !BGK && v.trt ? P.omega_m : P.omega, M(1));
     const M sp = X::fma(X::mul(M(9), cu), cF, X::mul(M(-3), uF));
     r = X::fma(w, X::fma(kp, sp, X::mul(X::mul(M(3), km), cF)), r);
   }
@@ -411,17 +415,27 @@ __device__ __forceinline__ M neq_regularized(int i, const M (&pi)[6], M ux, M uy
   return X::mul(dweight<L, M>(i), X::add(t2, t3));
 }
 
-template <class L, typename S, typename M>
-__device__ void boundary(const View &v, const RecSet &rs, const Rec &r, const M *fs, int stride,
-                         const Macro<L, M> &m, const M (&pi)[6], long long n, int x, int y, int z,
-                         S *__restrict__ fout) {
+// RULE >= 0: the rule is BC_ELIBB_F or BC_ELIBB_FQ under BGK with the bounce-back
+// wall non-equilibrium, known at compile time, so that the link loop carries no
+// run-time choice of rule; a static wall (u_w = 0) then also skips the
+// wall-velocity terms, f^eq_i(rho, 0) = w_i drho and no moving-wall term, which
+// the general form computes with zeros. RULE < 0: every rule, chosen at run time.
+// A node whose neighbours need no wrap finds its written-ahead slots at the
+// host's per-direction offsets (View::loff).
+template <class L, typename S, typename M, int RULE>
+__device__ __forceinline__ void boundary_rule(const View &v, const RecSet &rs, const Rec &r, const M *fs,
+                                              int stride, const Macro<L, M> &m, const M (&pi)[6], long long n,
+                                              int x, int y, int z, S *__restrict__ fout) {
   using X = Ex<M>;
+  constexpr bool SPEC = RULE >= 0;
+  const int bc = SPEC ? RULE : v.bc;
   const M *lq = static_cast<const M *>(rs.lq);
   const M *luw = static_cast<const M *>(rs.luw);
   const M *luw1 = static_cast<const M *>(rs.luw1);
   const Par<M> P(v);
   const uint32_t open = r.open & ~REC_MOVING;
   const bool moving = luw != nullptr && (r.open & REC_MOVING);
+  const bool interior = x > 0 && x < v.nx - 1 && y > 0 && y < v.ny - 1 && (L::D == 2 || (z > 0 && z < v.nz - 1));
   uint32_t links = r.cut | open;
 #pragma unroll 1
   while (links) {
@@ -438,59 +452,105 @@ __device__ void boundary(const View &v, const RecSet &rs, const Rec &r, const M 
     } else {
       const uint32_t li = r.link0 + __popc(r.cut & (bit - 1u));
       const M q = lq[li];
-      M wx = M(0), wy = M(0), wz = M(0), vx = M(0), vy = M(0), vz = M(0);
-      if (moving) {
-        wx = luw[3 * li]; wy = luw[3 * li + 1]; wz = luw[3 * li + 2];
-        vx = luw1[3 * li]; vy = luw1[3 * li + 1]; vz = luw1[3 * li + 2];
-      }
       const M w = dweight<L, M>(i);
-      const M me = X::mul(X::mul(X::mul(M(6), w), m.rho), cdot_r<L, M>(i, wx, wy, wz));
       const M fi = fs[i * stride];
-      const M g = X::add(post_r<L, M>(v, P, ib, fib, fi, m), me);
       const M q2 = X::mul(M(2), q);               // 2q (exact)
       const M a = X::sub(q2, M(1)), oma = X::sub(M(1), q2);  // 2q - 1, 1 - 2q
       const M omq = X::sub(M(1), q);              // 1 - q
-      if (v.bc == BC_HWBB || (q == M(0.5) && v.bc != BC_ELIBB_U)) {
-        val = g;
-      } else if (v.bc == BC_BFL) {
-        if (q < M(0.5)) {
-          val = (r.ffok & bit) ? X::fma(q2, g, X::mul(oma, me)) : g;
-        } else {
-          const M h = post_r<L, M>(v, P, i, fi, fib, m);
-          val = X::div(X::fma(a, h, g), q2);
-        }
-      } else {
-        // wall non-equilibrium: f^neq_ibar(x_F) (Eq. neqbb-s), or the regularized
-        // estimate with the wall velocity of each wall point's time (Eq. fi_neq)
+      if constexpr (SPEC) {
         const M fneq_ib = X::sub(fib, feq_r<L, M>(ib, m.drho, m.rho, m.ux, m.uy, m.uz, m.usq));
-        const bool reg = v.wall_neq != 0;
-        const M fn1 = reg ? neq_regularized<L, M>(i, pi, wx, wy, wz) : fneq_ib;
-        const M fn0 = reg ? neq_regularized<L, M>(i, pi, vx, vy, vz) : fneq_ib;
-        const M u0sq = X::fma(wz, wz, X::fma(wy, wy, X::mul(wx, wx)));
-        const M f1 = X::fma(X::sub(M(1), P.omega), fn1, feq_r<L, M>(i, m.drho, m.rho, wx, wy, wz, u0sq));
-        const bool unified_lin = v.bc == BC_ELIBB_U || (v.bc == BC_ELIBB_UQ && omq < P.qcut);
-        if (unified_lin || q < M(0.5) || v.bc == BC_ELIBB_UQ) {
+        M g = post_r<L, M, true>(v, P, ib, fib, fi, m), f0, f1;
+        if (moving) {
+          const M wx = luw[3 * li], wy = luw[3 * li + 1], wz = luw[3 * li + 2];
+          const M vx = luw1[3 * li], vy = luw1[3 * li + 1], vz = luw1[3 * li + 2];
+          g = X::add(g, X::mul(X::mul(X::mul(M(6), w), m.rho), cdot_r<L, M>(i, wx, wy, wz)));
+          const M u0sq = X::fma(wz, wz, X::fma(wy, wy, X::mul(wx, wx)));
           const M u1sq = X::fma(vz, vz, X::fma(vy, vy, X::mul(vx, vx)));
-          const M f0 = X::add(feq_r<L, M>(i, m.drho, m.rho, vx, vy, vz, u1sq), fn0);
-          if (unified_lin)  // ELIBB-U: the wall points s = 0 and s = 1 only
-            val = X::fma(q, f1, X::mul(omq, f0));
-          else if ((v.bc == BC_ELIBB_FQ && q >= P.qcut) || v.bc == BC_ELIBB_UQ)
+          f1 = X::fma(X::sub(M(1), P.omega), fneq_ib, feq_r<L, M>(i, m.drho, m.rho, wx, wy, wz, u0sq));
+          f0 = X::add(feq_r<L, M>(i, m.drho, m.rho, vx, vy, vz, u1sq), fneq_ib);
+        } else {
+          const M weq = X::mul(w, m.drho);  // f^eq_i(rho, 0), shifted
+          f1 = X::fma(X::sub(M(1), P.omega), fneq_ib, weq);
+          f0 = X::add(weq, fneq_ib);
+        }
+        if (q == M(0.5)) {
+          val = g;
+        } else if (q < M(0.5)) {
+          if (RULE == BC_ELIBB_FQ && q >= P.qcut)
             val = X::fma(a, f1, X::fma(oma, f0, g));                  // (1-2q) f0 + g + (2q-1) f1
           else
             val = X::div(X::fma(q, g, X::mul(oma, f0)), omq);         // ((1-2q) f0 + q g) / (1-q)
-        } else if (v.bc == BC_ELIBB_FQ) {
-          // ((1-q) g + 2 (2q-1) f1 + (2q-1)(q-1) h) / (2 q^2)
-          const M h = post_r<L, M>(v, P, i, fi, fib, m);
+        } else if (RULE == BC_ELIBB_FQ) {
+          const M h = post_r<L, M, true>(v, P, i, fi, fib, m);
           val = X::div(X::fma(X::mul(a, X::sub(q, M(1))), h, X::fma(X::mul(M(2), a), f1, X::mul(omq, g))),
                        X::mul(q2, q));
         } else {
           val = X::div(X::fma(a, f1, X::mul(omq, g)), q);              // ((1-q) g + (2q-1) f1) / q
         }
+      } else {
+        M wx = M(0), wy = M(0), wz = M(0), vx = M(0), vy = M(0), vz = M(0);
+        if (moving) {
+          wx = luw[3 * li]; wy = luw[3 * li + 1]; wz = luw[3 * li + 2];
+          vx = luw1[3 * li]; vy = luw1[3 * li + 1]; vz = luw1[3 * li + 2];
+        }
+        const M me = X::mul(X::mul(X::mul(M(6), w), m.rho), cdot_r<L, M>(i, wx, wy, wz));
+        const M g = X::add(post_r<L, M>(v, P, ib, fib, fi, m), me);
+        if (bc == BC_HWBB || (q == M(0.5) && bc != BC_ELIBB_U)) {
+          val = g;
+        } else if (bc == BC_BFL) {
+          if (q < M(0.5)) {
+            val = (r.ffok & bit) ? X::fma(q2, g, X::mul(oma, me)) : g;
+          } else {
+            const M h = post_r<L, M>(v, P, i, fi, fib, m);
+            val = X::div(X::fma(a, h, g), q2);
+          }
+        } else {
+          // wall non-equilibrium: f^neq_ibar(x_F) (Eq. neqbb-s), or the regularized
+          // estimate with the wall velocity of each wall point's time (Eq. fi_neq)
+          const M fneq_ib = X::sub(fib, feq_r<L, M>(ib, m.drho, m.rho, m.ux, m.uy, m.uz, m.usq));
+          const bool reg = v.wall_neq != 0;
+          const M fn1 = reg ? neq_regularized<L, M>(i, pi, wx, wy, wz) : fneq_ib;
+          const M fn0 = reg ? neq_regularized<L, M>(i, pi, vx, vy, vz) : fneq_ib;
+          const M u0sq = X::fma(wz, wz, X::fma(wy, wy, X::mul(wx, wx)));
+          const M f1 = X::fma(X::sub(M(1), P.omega), fn1, feq_r<L, M>(i, m.drho, m.rho, wx, wy, wz, u0sq));
+          const bool unified_lin = bc == BC_ELIBB_U || (bc == BC_ELIBB_UQ && omq < P.qcut);
+          if (unified_lin || q < M(0.5) || bc == BC_ELIBB_UQ) {
+            const M u1sq = X::fma(vz, vz, X::fma(vy, vy, X::mul(vx, vx)));
+            const M f0 = X::add(feq_r<L, M>(i, m.drho, m.rho, vx, vy, vz, u1sq), fn0);
+            if (unified_lin)  // ELIBB-U: the wall points s = 0 and s = 1 only
+              val = X::fma(q, f1, X::mul(omq, f0));
+            else if ((bc == BC_ELIBB_FQ && q >= P.qcut) || bc == BC_ELIBB_UQ)
+              val = X::fma(a, f1, X::fma(oma, f0, g));                  // (1-2q) f0 + g + (2q-1) f1
+            else
+              val = X::div(X::fma(q, g, X::mul(oma, f0)), omq);         // ((1-2q) f0 + q g) / (1-q)
+          } else if (bc == BC_ELIBB_FQ) {
+            // ((1-q) g + 2 (2q-1) f1 + (2q-1)(q-1) h) / (2 q^2)
+            const M h = post_r<L, M>(v, P, i, fi, fib, m);
+            val = X::div(X::fma(X::mul(a, X::sub(q, M(1))), h, X::fma(X::mul(M(2), a), f1, X::mul(omq, g))),
+                         X::mul(q2, q));
+          } else {
+            val = X::div(X::fma(a, f1, X::mul(omq, g)), q);              // ((1-q) g + (2q-1) f1) / q
+          }
+        }
       }
     }
-    fout[(long long)i * v.np + n + upstream_offset(v, x, y, z, dcx<L>(i), dcy<L>(i), dcz<L>(i))] =
-        to_store<S, M>(val);
+    const long long slot = interior ? (long long)v.loff[i] + n
+                                    : (long long)i * v.np + n + upstream_offset(v, x, y, z, dcx<L>(i), dcy<L>(i), dcz<L>(i));
+    fout[slot] = to_store<S, M>(val);
   }
+}
+
+template <class L, typename S, typename M>
+__device__ void boundary(const View &v, const RecSet &rs, const Rec &r, const M *fs, int stride,
+                         const Macro<L, M> &m, const M (&pi)[6], long long n, int x, int y, int z,
+                         S *__restrict__ fout) {
+  const bool bgk_bb = !v.trt && !v.wall_neq;
+  if (bgk_bb && v.bc == BC_ELIBB_F)
+    boundary_rule<L, S, M, BC_ELIBB_F>(v, rs, r, fs, stride, m, pi, n, x, y, z, fout);
+  else if (bgk_bb && v.bc == BC_ELIBB_FQ)
+    boundary_rule<L, S, M, BC_ELIBB_FQ>(v, rs, r, fs, stride, m, pi, n, x, y, z, fout);
+  else
+    boundary_rule<L, S, M, -1>(v, rs, r, fs, stride, m, pi, n, x, y, z, fout);
 }
 
 // non-binding request to bring the line holding p into L1
