@@ -25,6 +25,7 @@ import argparse
 import hashlib
 import json
 import os
+import socket
 import statistics
 import subprocess
 import sys
@@ -54,6 +55,8 @@ def parse():
     ap.add_argument("--launch", default=None, help="bx,by,variant,tiles of the step kernel (default: autotune)")
     ap.add_argument("--tune-steps", type=int, default=20)
     ap.add_argument("--no-extras", action="store_true", help="skip the FP16/BF16 and batched measurements")
+    ap.add_argument("--record", default=None,
+                    help="also append the JSON line, with the time and host, to this JSON-lines file")
     return ap.parse_args()
 
 
@@ -121,10 +124,11 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(dtype):
-    """DRAM bytes per k_step launch from the committed ncu summary, if it was taken
-    on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", f"k_step_d3q19_{dtype}_sphere_duct.json")
+def profiled_traffic(name):
+    """DRAM bytes per launch of a step kernel at the bench's full size, from the
+    committed ncu summary profiles/<name>.json, if it was taken on the current
+    kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"{name}.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
@@ -265,6 +269,7 @@ def dtype_variant(torch, lbm, W, dtype, steps, peak):
     out = {"value": round(nfluid * steps / (ms * 1e-3) / 1e6, 2), "unit": "MLUPS", "steps": steps,
            "best_of": 5, "ms_per_step": round(ms / steps, 5), "launch": tuned}
     out.update(roofline_of(nfluid, padded_nodes(wl["dims"]), nb, nwall, 19, dtype, False, ms / steps, peak))
+    out["traffic"] = profiled_traffic(f"k_step_d3q19_{dtype}_sphere_duct")
     return out
 
 
@@ -293,6 +298,7 @@ def porous_moving(torch, lbm, W, dtype, steps, peak):
            "finite": finite, "ms_per_step": round(ms / steps, 4), "launch": tuned,
            "roofline_note": "static geometry's bytes; the moving sphere's few links add under 0.1 %"}
     out.update(roofline_of(nfluid, padded_nodes(wl["dims"]), nb, nwall, 19, dtype, False, ms / steps, peak))
+    out["traffic"] = profiled_traffic(f"k_step_d3q19_{dtype}_porous_moving")
     return out
 
 
@@ -341,6 +347,8 @@ def batched_vs_plain(torch, lbm, W, regime, dtype, steps, peak):
     rf = roofline_of(nfluid, sum(padded_nodes(w["dims"]) for w in wls), sum(x[1] for x in c),
                      sum(x[2] for x in c), 19, dtype, False, ms_b / steps, peak)
     out.update({"batched_" + k: v for k, v in rf.items()})
+    if regime == "large":
+        out["batched_traffic"] = profiled_traffic(f"k_step_batch_d3q19_{dtype}_batched_ducts")
     return out
 
 
@@ -429,7 +437,7 @@ def reference_arm(args, rank, dist):
             "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": cores_used(), "kind": "oracle",
                              "sample": f"{steps} full-size steps of {WORKLOAD} (FP64 oracle, OpenMP)"},
             "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    emit(args, line)
     return 0
 
 
@@ -483,7 +491,7 @@ def ours_arm(args, rank, world, dist):
     ls = 8 if args.dtype == "f64" else 4
     abytes = algorithmic_bytes(nfluid, np_, nb, nwall, 19, s_bytes, ls, False)
     achieved = abytes / (ms_step * 1e-3) / 1e9
-    traffic = profiled_traffic(args.dtype)
+    traffic = profiled_traffic(f"k_step_d3q19_{args.dtype}_sphere_duct")
     # ---- end to end through the public API: upload the state from pinned host memory,
     # then per step lbm_step(1) and a synchronising read of the drag force (24 B)
     K2 = 1000
@@ -578,8 +586,18 @@ def ours_arm(args, rank, world, dist):
         "accuracy": accuracy,
         "variants": extras,
     }
-    print(json.dumps(line), flush=True)
+    emit(args, line)
     return 0
+
+
+def emit(args, line):
+    """Print the result line; with --record also append it to a JSON-lines run log,
+    stamped with the UTC time and the host name."""
+    print(json.dumps(line), flush=True)
+    if args.record:
+        rec = dict(line, recorded_utc=time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()), host=socket.gethostname())
+        with open(args.record, "a") as fh:
+            fh.write(json.dumps(rec) + "\n")
 
 
 def main():

@@ -351,9 +351,11 @@ int lbm_set_wait_limit(lbm_handle h, long long polls);
  *     copies, several tiles ahead, and the block computes from there. FP32,
  *     FP16 and BF16 only;
  *   variant 5..7: two nodes per thread along x, with vector loads and stores,
- *     at least 1..3 resident blocks per SM. A block covers 2*bx nodes of a row,
- *     which must divide the padded row. FP32/FP16/BF16, not with BFL (switching
- *     to BFL moves the launch back to variant 0);
+ *     at least 1..3 resident 256-thread blocks per SM. A block covers 2*bx nodes
+ *     of a row, which must divide the padded row. FP32/FP16/BF16, not with BFL
+ *     (switching to BFL moves the launch back to variant 0);
+ *   variant 8: as 5..7, for blocks of exactly 128 threads, at least 7 resident
+ *     per SM (72 registers a thread);
  *   tiles 1..4: consecutive entries of the step kernel's tile table that one
  *     block processes. The table lists, plane by plane, the lattice tiles and
  *     then the boundary-record tiles.

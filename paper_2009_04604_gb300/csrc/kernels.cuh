@@ -580,10 +580,15 @@ __device__ __forceinline__ void boundary_node(const View &v, const RecSet &rs, c
       prefetch_l1(static_cast<const M *>(rs.luw1) + 3 * l1 + 2);
     }
   }
-  Nbr nb;
-  nb.init(v, x, y, z);
   M f[L::Q];
-  gather<L, S, M>(v, fin, n, nb, f);
+  if (x > 0 && x < v.nx - 1 && y > 0 && y < v.ny - 1 && (L::D == 2 || (z > 0 && z < v.nz - 1))) {
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) f[i] = to_math<S, M>(__ldg(fin + (v.loff[i] + n)));
+  } else {
+    Nbr nb;
+    nb.init(v, x, y, z);
+    gather<L, S, M>(v, fin, n, nb, f);
+  }
   if (v.bc == BC_BFL) bfl_complete<L, M>(v, r, f);
   const Macro<L, M> m = moments<L, M>(v, f);
   M pi[6] = {M(0), M(0), M(0), M(0), M(0), M(0)};
@@ -606,14 +611,29 @@ __device__ __forceinline__ void boundary_node(const View &v, const RecSet &rs, c
   boundary<L, S, M>(v, rs, r, fs, stride, m, pi, n, x, y, z, fout);
 }
 
-// Column and row of lattice tile t in its plane, t / gx by one wide multiply and
-// a shift (division by an invariant integer, Granlund and Montgomery): with
-// l = floor(log2 gx), gx_m = ceil(2^(32+l) / gx) < 2^32 and gx_s = 32 + l, or
-// gx_m = 2^31 and gx_s = 31 + l when gx is a power of two. The error of the
-// product is below t / 2^(32+l) < 1 / (2 gx) for t < 2^31, so the quotient is exact.
+// Quotients by divisors fixed for a run (the tiles per row gx, the padded row
+// nxp, the plane nxp ny): t / d by one wide multiply and a shift (division by an
+// invariant integer, Granlund and Montgomery). With l = floor(log2 d) the host
+// sets m = ceil(2^(32+l) / d) < 2^32 and s = 32 + l, or m = 2^31 and s = 31 + l
+// when d is a power of two. The error of the product is below
+// t / 2^(32+l) < 1 / (2 d) for t < 2^31, so the quotient is exact.
+__device__ __forceinline__ int div_by(int t, uint32_t m, uint32_t s) {
+  return (int)(((unsigned long long)(unsigned)t * m) >> s);
+}
+
+// column and row of lattice tile t in its plane
 __device__ __forceinline__ int2 tile_coords(const View &v, int t) {
-  const int ty = (int)(((unsigned long long)(unsigned)t * v.gx_m) >> v.gx_s);
+  const int ty = div_by(t, v.gx_m, v.gx_s);
   return make_int2(t - ty * v.gx, ty);
+}
+
+// x, y, z of padded node n (n < 2^31), with the same multiply-and-shift quotients
+// by nxp and nxp ny
+__device__ __forceinline__ int3 node_coords(const View &v, int n) {
+  const int z = div_by(n, v.pl_m, v.pl_s);
+  const int r = n - z * v.nxp * v.ny;
+  const int y = div_by(r, v.nxp_m, v.nxp_s);
+  return make_int3(r - y * v.nxp, y, z);
 }
 
 // ---------------------------------------------------------------- the fused step
@@ -859,15 +879,16 @@ __device__ __forceinline__ void boundary_tile(const View &v, const S *__restrict
   const int rid = tile.y + t;
   const Rec r = rs.rec[rid];
   const int n = (int)rs.rnode[rid];
-  const int x = n % v.nxp, y = (n / v.nxp) % v.ny, z = n / (v.nxp * v.ny);
-  boundary_node<L, S, M>(v, rs, r, fin, fout, n, x, y, z, stage + t, stage_threads<L, M>());
+  const int3 c = node_coords(v, n);
+  boundary_node<L, S, M>(v, rs, r, fin, fout, n, c.x, c.y, c.z, stage + t, stage_threads<L, M>());
 }
 
 // Block b takes table entries b*T .. b*T+T-1 (T = v.tpb_tiles <= 4), whose
-// descriptors it loads together up front.
-template <class L, typename S, typename M, int MINB, int PHYS, bool PAIR = false>
-__global__ void __launch_bounds__(256, MINB) k_step(const View v, const S *__restrict__ fin,
-                                                    S *__restrict__ fout) {
+// descriptors it loads together up front. MAXT: the largest block the register
+// budget is set for (MINB resident blocks of MAXT threads).
+template <class L, typename S, typename M, int MINB, int PHYS, bool PAIR = false, int MAXT = 256>
+__global__ void __launch_bounds__(MAXT, MINB) k_step(const View v, const S *__restrict__ fin,
+                                                     S *__restrict__ fout) {
   __shared__ M stage[L::Q * stage_threads<L, M>()];  // boundary tiles: populations, [direction][thread]
   const int T = v.tpb_tiles;
   const int first = blockIdx.x * T;

@@ -198,6 +198,8 @@ struct View {
   const int2 *tiles;         // step-kernel block table (see k_step)
   int gx;                    // lattice tiles per row of tiles (nxp / block x)
   uint32_t gx_m, gx_s;       // t / gx = (t gx_m) >> gx_s for 0 <= t < 2^31 (tile_coords)
+  uint32_t nxp_m, nxp_s;     // n / nxp, the same way (node_coords)
+  uint32_t pl_m, pl_s;       // n / (nxp ny), the same way
   // per-direction element offsets, computed on the host so that the kernels use
   // them as constant operands: soff[i] = i np (plane i), loff[i] = i np - (c_ix +
   // c_iy nxp + c_iz nxp ny) (the source of population i at an interior node)

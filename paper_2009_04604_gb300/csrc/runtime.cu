@@ -268,6 +268,17 @@ extern "C" int lbm_set_collision(lbm_handle h, int model, double magic) {
 }
 
 // ---------------------------------------------------------------- kernel view, launch shapes
+// Multiplier and shift of the quotient t / d by one wide multiply (div_by in
+// kernels.cuh): l = floor(log2 d), m = ceil(2^(32+l) / d) and s = 32 + l, or
+// m = 2^31 and s = 31 + l for a power of two.
+static void invariant_divisor(long long dd, uint32_t *m, uint32_t *s) {
+  const unsigned long long d = (unsigned long long)(dd > 0 ? dd : 1);
+  unsigned l = 0;
+  while ((2ull << l) <= d) ++l;
+  if ((d & (d - 1)) == 0) { *m = 1u << 31; *s = 31 + l; }
+  else { *m = (uint32_t)(((1ull << (32 + l)) + d - 1) / d); *s = 32 + l; }
+}
+
 View lbm_sim::view() const {
   View v;
   v.nx = nx; v.ny = ny; v.nz = nz; v.nxp = nxp; v.np = np;
@@ -289,13 +300,9 @@ View lbm_sim::view() const {
   v.err = err_dev;
   v.wait_limit = wait_limit;
   v.tiles = tiles; v.gx = nxp / (step_bx * npt());
-  {  // multiplier and shift of t / gx (tile_coords): l = floor(log2 gx)
-    const unsigned d = (unsigned)(v.gx > 0 ? v.gx : 1);
-    unsigned l = 0;
-    while ((2ull << l) <= d) ++l;
-    if ((d & (d - 1)) == 0) { v.gx_m = 1u << 31; v.gx_s = 31 + l; }
-    else { v.gx_m = (uint32_t)(((1ull << (32 + l)) + d - 1) / d); v.gx_s = 32 + l; }
-  }
+  invariant_divisor(v.gx, &v.gx_m, &v.gx_s);
+  invariant_divisor(nxp, &v.nxp_m, &v.nxp_s);
+  invariant_divisor((long long)nxp * ny, &v.pl_m, &v.pl_s);
   for (int i = 0; i < Q; ++i) {
     int c[3];
     lattice_c(i, c[0], c[1], c[2]);
@@ -680,7 +687,8 @@ int lbm_sim::download(HostGeometry &g) {
 // ---------------------------------------------------------------- launch configuration
 static bool valid_launch(const lbm_sim *h, int bx, int by, int variant, int tiles) {
   if (bx < 32 || bx % 32 || h->nxp % bx || by < 1 || bx * by > 256) return false;
-  if (variant < 0 || variant > 7 || tiles < 1 || tiles > 4) return false;
+  if (variant < 0 || variant > 8 || tiles < 1 || tiles > 4) return false;
+  if (variant == 8 && bx * by != 128) return false;  // compiled for blocks of 128 threads
   if (h->dtype == LBM_F64 && variant != 0) return false;
   if (h->dtype == LBM_F64 && h->lattice == LBM_D3Q27 && bx * by > 128) return false;  // shared staging
   if (variant >= 5 && (h->nxp % (2 * bx) || h->bc == LBM_BC_BFL)) return false;  // pairs: whole rows, no BFL
@@ -719,7 +727,7 @@ extern "C" int lbm_autotune(lbm_handle h, int steps, int *bx, int *by, int *vari
   int best[4] = {save[0], save[1], save[2], save[3]};
   float best_ms = 1e30f;
   int rc = LBM_OK;
-  const int nvar = h->dtype == LBM_F64 ? 1 : 8;  // 4: TMA-staged persistent kernel; 5-7: node pairs
+  const int nvar = h->dtype == LBM_F64 ? 1 : 9;  // 4: TMA-staged persistent kernel; 5-8: node pairs
   const int tile_opts[3] = {1, 2, 4};
   for (int threads = 128; threads <= 256 && rc == LBM_OK; threads *= 2)
     for (int bxx = 32; bxx <= threads && rc == LBM_OK; bxx *= 2) {

@@ -16,17 +16,17 @@ namespace lbm {
 inline int phys_of(const View &v) { return (v.has_force ? PH_FORCE : 0) | (v.trt ? PH_TRT : 0); }
 
 // The step grid is 1-D, one block per entry of the tile table (l.grid.x entries).
-template <class L, typename S, typename M, int MINB, bool PAIR = false>
+template <class L, typename S, typename M, int MINB, bool PAIR = false, int MAXT = 256>
 cudaError_t step_variant(const View &v, const void *fin, void *fout, const Launch &l) {
   const S *a = static_cast<const S *>(fin);
   S *b = static_cast<S *>(fout);
   switch (phys_of(v)) {
-    case PH_FORCE: k_step<L, S, M, MINB, PH_FORCE, PAIR><<<l.grid, l.block, 0, l.stream>>>(v, a, b); break;
-    case PH_TRT: k_step<L, S, M, MINB, PH_TRT, PAIR><<<l.grid, l.block, 0, l.stream>>>(v, a, b); break;
+    case PH_FORCE: k_step<L, S, M, MINB, PH_FORCE, PAIR, MAXT><<<l.grid, l.block, 0, l.stream>>>(v, a, b); break;
+    case PH_TRT: k_step<L, S, M, MINB, PH_TRT, PAIR, MAXT><<<l.grid, l.block, 0, l.stream>>>(v, a, b); break;
     case PH_FORCE | PH_TRT:
-      k_step<L, S, M, MINB, PH_FORCE | PH_TRT, PAIR><<<l.grid, l.block, 0, l.stream>>>(v, a, b);
+      k_step<L, S, M, MINB, PH_FORCE | PH_TRT, PAIR, MAXT><<<l.grid, l.block, 0, l.stream>>>(v, a, b);
       break;
-    default: k_step<L, S, M, MINB, 0, PAIR><<<l.grid, l.block, 0, l.stream>>>(v, a, b); break;
+    default: k_step<L, S, M, MINB, 0, PAIR, MAXT><<<l.grid, l.block, 0, l.stream>>>(v, a, b); break;
   }
   return cudaGetLastError();
 }
@@ -111,6 +111,7 @@ cudaError_t launch_step_ls(int variant, const View &v, const void *fin, void *fo
       case 5: return step_variant<L, S, M, 1, true>(v, fin, fout, l);
       case 6: return step_variant<L, S, M, 2, true>(v, fin, fout, l);
       case 7: return step_variant<L, S, M, 3, true>(v, fin, fout, l);
+      case 8: return step_variant<L, S, M, 7, true, 128>(v, fin, fout, l);
       default: return step_variant<L, S, M, 1>(v, fin, fout, l);
     }
   }

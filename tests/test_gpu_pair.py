@@ -1,4 +1,4 @@
-"""The two-nodes-per-thread step kernel (launch variants 5..7) gives the
+"""The two-nodes-per-thread step kernel (launch variants 5..8) gives the
 populations of the one-node-per-thread kernel (variant 0). The per-node
 arithmetic is the same; only the loads (vector loads plus warp shuffles for the
 x-shifted planes) and the stores differ. The compiler may still fuse
@@ -65,7 +65,7 @@ def _make(case, dtype):
     return s
 
 
-VARIANT = {"duct": 5, "random3d": 6, "random2d_shear": 7, "periodic": 5, "moving": 6}
+VARIANT = {"duct": 5, "random3d": 6, "random2d_shear": 7, "periodic": 8, "moving": 8}
 
 
 @pytest.mark.parametrize("dtype", [lbm.F32, lbm.F16, lbm.BF16])
@@ -73,7 +73,7 @@ VARIANT = {"duct": 5, "random3d": 6, "random2d_shear": 7, "periodic": 5, "moving
 def test_pair_variant_matches_register_variant(case, dtype):
     a, b = _make(case, dtype), _make(case, dtype)
     a.set_launch(32, 8, 0, 1)
-    b.set_launch(32, 4, VARIANT[case], 2)  # 64 nodes of a row per warp
+    b.set_launch(32, 4, VARIANT[case], 2)  # 64 nodes of a row per warp, 128 threads a block
     for n in (3, 40):  # direct launches, then a graph replay
         a.step(n)
         b.step(n)
@@ -93,6 +93,9 @@ def test_pair_variant_limits():
     s = _make("random3d", lbm.F32)  # padded row of 64 nodes
     with pytest.raises(lbm.LBMError):  # a block row must cover whole pairs of the padded row
         s.set_launch(64, 4, 5, 1)
+    with pytest.raises(lbm.LBMError):  # variant 8 is compiled for blocks of 128 threads
+        s.set_launch(32, 8, 8, 1)
+    s.set_launch(32, 4, 8, 1)
     s.set_launch(32, 8, 6, 1)
     s.set_options(lbm.BC_BFL, 1.0, (0, 0, 0), 0)  # BFL moves the launch back to variant 0
     assert s.get_launch()[2] == 0

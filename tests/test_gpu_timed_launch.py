@@ -1,8 +1,9 @@
 """Parity with the FP64 oracle at the launch configurations the benchmark times.
 
 The full-size sphere duct runs FP32 storage with 128 x 1 threads, two nodes per
-thread (variant 7), one tile per block, and FP16/BF16 storage with 32 x 4
-threads, one node per thread (variant 3), two tiles per block. These tests run
+thread (variant 7, or variant 8 with its 72-register budget), one tile per
+block, and FP16/BF16 storage with 32 x 4 threads, one node per thread
+(variant 3), two tiles per block. These tests run
 exactly those launches on a duct whose padded rows hold 256 nodes, so that the
 two-nodes-per-thread blocks cover whole rows as in the benchmark: 256 x 24 x 24,
 velocity inlet u = 0.02, pressure outlet, side walls, a sphere of radius 5, BGK
@@ -75,6 +76,8 @@ CASES = [
     (lbm.BC_ELIBB_FQ, lbm.F64, (128, 2, 0, 1)),
     (lbm.BC_ELIBB_F, lbm.F32, (128, 1, 7, 1)),
     (lbm.BC_ELIBB_FQ, lbm.F32, (128, 1, 7, 1)),
+    (lbm.BC_ELIBB_F, lbm.F32, (128, 1, 8, 1)),
+    (lbm.BC_ELIBB_F, lbm.F16, (128, 1, 8, 1)),
     (lbm.BC_ELIBB_F, lbm.F32, (128, 2, 4, 1)),
     (lbm.BC_BFL, lbm.F32, (128, 2, 3, 1)),
     (lbm.BC_ELIBB_F, lbm.F16, (32, 4, 3, 2)),

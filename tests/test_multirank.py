@@ -55,3 +55,21 @@ def test_two_gloo_ranks_time_by_the_slowest_and_count_every_rank(tmp_path):
         assert r["ms"] == 15.0                      # the slowest rank's time, on every rank
         assert abs(r["value"] - 2 * 1000 * 10 / 0.015 / 1e6) < 1e-12
     assert res[1]["rc"] == 0 and res[1]["printed"] == ""  # no oracle work, no line, off rank 0
+
+
+def test_bench_run_record_appends_a_json_line(tmp_path, capsys):
+    """bench.py --record: the printed line is also appended, with time and host,
+    to a JSON-lines run log; a second run appends a second line."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import argparse
+    import bench
+    log = tmp_path / "runs.jsonl"
+    args = argparse.Namespace(record=str(log))
+    bench.emit(args, {"metric": "m", "value": 1.5})
+    bench.emit(args, {"metric": "m", "value": 2.5})
+    printed = [json.loads(x) for x in capsys.readouterr().out.strip().splitlines()]
+    assert [p["value"] for p in printed] == [1.5, 2.5]
+    recs = [json.loads(x) for x in log.read_text().splitlines()]
+    assert [r["value"] for r in recs] == [1.5, 2.5]
+    assert all("recorded_utc" in r and r["host"] == socket.gethostname() for r in recs)
