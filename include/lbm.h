@@ -78,7 +78,8 @@ enum lbm_status {
   LBM_ERR_OOM = -3,       /* device allocation failed */
   LBM_ERR_NONFINITE = -4, /* a reduction found NaN or Inf in the state */
   LBM_ERR_TIMEOUT = -5,   /* a bounded device wait ran out */
-  LBM_ERR_STATE = -6      /* call out of order, e.g. stepping before set_geometry */
+  LBM_ERR_STATE = -6,     /* call out of order, e.g. stepping before set_geometry */
+  LBM_ERR_BOUNDS = -7     /* debug builds: a population index out of range (not accessed) */
 };
 
 /* Analytic shapes for lbm_build_geometry. A node is solid where the shape's test
@@ -340,6 +341,22 @@ int lbm_load(lbm_handle h, const void *buf, size_t bytes);
  * the word. The state is then incomplete: re-initialise it. The paper has no
  * counterpart. */
 int lbm_set_wait_limit(lbm_handle h, long long polls);
+
+/* Bounds-checked builds. A library compiled with LBM_DEBUG checks every element
+ * index of a population load or store in the step, set-up, read-out and force
+ * kernels against [0, limit), limit = Q x padded nodes (the buffer's size) by
+ * default. An index outside is not accessed (a load reads 0); the first one, with
+ * the source line of the access, is kept in a device word per handle, and the
+ * next lbm_synchronize returns LBM_ERR_BOUNDS and clears it. The state is then
+ * wrong: re-initialise it. The paper has no counterpart; this stands in for a
+ * memory checker.
+ * lbm_is_debug_build: 1 for such a build, 0 otherwise.
+ * lbm_set_debug_limit: testing aid, sets the limit (negative: the default); a
+ * limit below the buffer's size makes accesses inside the buffer count as out of
+ * range, which exercises the checks without touching memory outside the
+ * buffers. LBM_ERR_STATE in a build without LBM_DEBUG. */
+int lbm_is_debug_build(void);
+int lbm_set_debug_limit(lbm_handle h, long long elements);
 
 /* Launch configuration of the step kernel:
  *   bx x by threads per block: bx a multiple of 32 that divides the padded row

@@ -32,12 +32,63 @@ namespace lbm {
 enum { BC_ELIBB_F = 0, BC_ELIBB_FQ = 1, BC_BFL = 2, BC_HWBB = 3, BC_ELIBB_U = 4, BC_ELIBB_UQ = 5 };
 
 // ---------------------------------------------------------------- gather
+// ---------------------------------------------------------------- population accesses
+// The step kernels load and store population buffers through LD_POP / ST_POP. A build with LBM_DEBUG checks every
+// index against [0, v.dbg_limit) first: the buffer's Q x padded nodes, or a
+// smaller limit set by lbm_set_debug_limit. An index outside is not accessed (a
+// load reads 0), and the first one is recorded in the device word *v.dbg as
+// (source line << 40) | (index mod 2^40), which lbm_synchronize reports as
+// LBM_ERR_BOUNDS. Without LBM_DEBUG the check compiles away.
+__device__ __forceinline__ bool pop_index_ok(const View &v, long long idx, int line) {
+#ifdef LBM_DEBUG
+  if (idx >= 0 && idx < v.dbg_limit) return true;
+  atomicCAS(v.dbg, 0ull, ((unsigned long long)line << 40) | ((unsigned long long)idx & ((1ull << 40) - 1ull)));
+  return false;
+#else
+  (void)v;
+  (void)idx;
+  (void)line;
+  return true;
+#endif
+}
+template <typename T>
+__device__ __forceinline__ T ld_pop(const View &v, const T *base, long long idx, int line) {
+  return pop_index_ok(v, idx, line) ? __ldg(base + idx) : T{};
+}
+// a vector of two consecutive elements idx, idx + 1 (V: float2, __half2, ...)
+template <typename V, typename T>
+__device__ __forceinline__ V ld_pop2(const View &v, const T *base, long long idx, int line) {
+  return pop_index_ok(v, idx, line) && pop_index_ok(v, idx + 1, line)
+             ? __ldg(reinterpret_cast<const V *>(base + idx))
+             : V{};
+}
+template <typename T>
+__device__ __forceinline__ void st_pop(const View &v, T *base, long long idx, T val, int line) {
+  if (pop_index_ok(v, idx, line)) base[idx] = val;
+}
+template <typename V, typename T>
+__device__ __forceinline__ void st_pop2(const View &v, T *base, long long idx, V val, int line) {
+  if (pop_index_ok(v, idx, line) && pop_index_ok(v, idx + 1, line)) *reinterpret_cast<V *>(base + idx) = val;
+}
+// The access is written as its pointer expression; base is the buffer's start.
+#ifdef LBM_DEBUG
+#define LD_POP(v, base, ptr) ld_pop((v), (base), (long long)((ptr) - (base)), __LINE__)
+#define LD_POP2(V, v, base, ptr) ld_pop2<V>((v), (base), (long long)((ptr) - (base)), __LINE__)
+#define ST_POP(v, base, ptr, ...) st_pop((v), (base), (long long)((ptr) - (base)), (__VA_ARGS__), __LINE__)
+#define ST_POP2(v, base, ptr, ...) st_pop2((v), (base), (long long)((ptr) - (base)), (__VA_ARGS__), __LINE__)
+#else  // the plain access, compiled exactly as written
+#define LD_POP(v, base, ptr) __ldg(ptr)
+#define LD_POP2(V, v, base, ptr) __ldg(reinterpret_cast<const V *>(ptr))
+#define ST_POP(v, base, ptr, ...) (*(ptr) = (__VA_ARGS__))
+#define ST_POP2(v, base, ptr, ...) (*reinterpret_cast<decltype(__VA_ARGS__) *>(ptr) = (__VA_ARGS__))
+#endif
+
 template <class L, typename S, typename M>
 __device__ __forceinline__ void gather(const View &v, const S *__restrict__ fin, long long n,
                                        const Nbr &nb, M (&f)[L::Q]) {
 #pragma unroll
   for (int i = 0; i < L::Q; ++i)
-    f[i] = to_math<S, M>(__ldg(fin + (long long)i * v.np + n + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))));
+    f[i] = to_math<S, M>(LD_POP(v, fin, fin + (long long)i * v.np + n + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))));
 }
 
 // BFL, q < 1/2: complete the written-ahead part with (1-2q) f*_ibar(x_FF, t),
@@ -267,9 +318,9 @@ __device__ __forceinline__ void relax(const View &v, const M (&f)[L::Q], const M
 // skip: planes not to store (bit i); 0 for fluid nodes.
 template <class L, typename S, typename M, int PHYS>
 __device__ __forceinline__ void collide_store(const View &v, const M (&f)[L::Q], const Macro<L, M> &m,
-                                              S *__restrict__ dst, int np, uint32_t skip) {
+                                              S *__restrict__ fout, int n, int np, uint32_t skip) {
   relax<L, M, PHYS, Units<S>::kStored>(v, f, m, [&](int i, M val) {
-    if (!((skip >> i) & 1u)) dst[i * np] = Units<S>::template store<M>(val);
+    if (!((skip >> i) & 1u)) ST_POP(v, fout, fout + n + i * np, Units<S>::template store<M>(val));
   });
 }
 
@@ -278,7 +329,7 @@ template <class L, typename S, typename M, int PHYS>
 __device__ __forceinline__ void collide_store_at(const View &v, const M (&f)[L::Q], const Macro<L, M> &m,
                                                  S *__restrict__ fout, int n, uint32_t skip) {
   relax<L, M, PHYS, Units<S>::kStored>(v, f, m, [&](int i, M val) {
-    if (!((skip >> i) & 1u)) fout[v.soff[i] + n] = Units<S>::template store<M>(val);
+    if (!((skip >> i) & 1u)) ST_POP(v, fout, &fout[v.soff[i] + n], Units<S>::template store<M>(val));
   });
 }
 
@@ -536,7 +587,7 @@ __device__ __forceinline__ void boundary_rule(const View &v, const RecSet &rs, c
     }
     const long long slot = interior ? (long long)v.loff[i] + n
                                     : (long long)i * v.np + n + upstream_offset(v, x, y, z, dcx<L>(i), dcy<L>(i), dcz<L>(i));
-    fout[slot] = to_store<S, M>(val);
+    ST_POP(v, fout, &fout[slot], to_store<S, M>(val));
   }
 }
 
@@ -583,7 +634,7 @@ __device__ __forceinline__ void boundary_node(const View &v, const RecSet &rs, c
   M f[L::Q];
   if (x > 0 && x < v.nx - 1 && y > 0 && y < v.ny - 1 && (L::D == 2 || (z > 0 && z < v.nz - 1))) {
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) f[i] = to_math<S, M>(__ldg(fin + (v.loff[i] + n)));
+    for (int i = 0; i < L::Q; ++i) f[i] = to_math<S, M>(LD_POP(v, fin, fin + (v.loff[i] + n)));
   } else {
     Nbr nb;
     nb.init(v, x, y, z);
@@ -605,7 +656,7 @@ __device__ __forceinline__ void boundary_node(const View &v, const RecSet &rs, c
     for (int i = 0; i < L::Q; ++i) {
       const int ib = opp<L>(i);
       if ((r.shell >> ib) & 1u) continue;
-      fout[v.soff[i] + n] = to_store<S, M>(post_r<L, M>(v, P, i, fs[i * stride], fs[ib * stride], m));
+      ST_POP(v, fout, &fout[v.soff[i] + n], to_store<S, M>(post_r<L, M>(v, P, i, fs[i * stride], fs[ib * stride], m)));
     }
   }
   boundary<L, S, M>(v, rs, r, fs, stride, m, pi, n, x, y, z, fout);
@@ -690,14 +741,14 @@ __device__ __forceinline__ void lattice_tile(const View &v, const S *__restrict_
       // no wrap: the source of population i is n - c_i, at an offset that is the
       // same for every thread and precomputed on the host (loff)
 #pragma unroll
-      for (int i = 0; i < L::Q; ++i) f[i] = Units<S>::template load<M>(__ldg(fin + (v.loff[i] + n)));
+      for (int i = 0; i < L::Q; ++i) f[i] = Units<S>::template load<M>(LD_POP(v, fin, fin + (v.loff[i] + n)));
     } else {
       Nbr nb;
       nb.init(v, x, y, z);
       const S *__restrict__ src = fin + n;
 #pragma unroll
       for (int i = 0; i < L::Q; ++i)
-        f[i] = Units<S>::template load<M>(__ldg(src + (i * np + nb.at(-L::cx(i), -L::cy(i), -L::cz(i)))));
+        f[i] = Units<S>::template load<M>(LD_POP(v, fin, src + (i * np + nb.at(-L::cx(i), -L::cy(i), -L::cz(i)))));
     }
     if (v.bc == BC_BFL && (fl & F_BOUNDARY)) bfl_complete<L, M>(v, *record_of(v, n, bal), f);
   } else {
@@ -782,7 +833,7 @@ __device__ __forceinline__ void lattice_tile_pair(const View &v, const S *__rest
   T p[L::Q];
 #pragma unroll
   for (int i = 0; i < L::Q; ++i)
-    p[i] = __ldg(reinterpret_cast<const T *>(fin + (v.soff[i] + n + ro[1 - L::cy(i)][1 - L::cz(i)])));
+    p[i] = LD_POP2(T, v, fin, fin + (v.soff[i] + n + ro[1 - L::cy(i)][1 - L::cz(i)]));
   // the element per x-shifted plane that the neighbouring lanes cannot supply:
   // c_ix = +1: x-1 at lane 0 (wrapping when x = 0); c_ix = -1: x+1 when it leaves
   // the row (node x+1 is then padding), else x+2 at lane 31 or when it wraps
@@ -799,11 +850,11 @@ __device__ __forceinline__ void lattice_tile_pair(const View &v, const S *__rest
       e[i] = M(0);
       if (cx > 0 && need_up)
         e[i] = Units<S>::template load<M>(
-            __ldg(fin + (long long)i * np + n + upstream_offset(v, x, y, z, cx, L::cy(i), L::cz(i))));
+            LD_POP(v, fin, fin + (long long)i * np + n + upstream_offset(v, x, y, z, cx, L::cy(i), L::cz(i))));
       if (cx < 0 && need_dn) {
         const int off = wa ? upstream_offset(v, x, y, z, cx, L::cy(i), L::cz(i))
                            : 1 + upstream_offset(v, x + 1, y, z, cx, L::cy(i), L::cz(i));
-        e[i] = Units<S>::template load<M>(__ldg(fin + (long long)i * np + n + off));
+        e[i] = Units<S>::template load<M>(LD_POP(v, fin, fin + (long long)i * np + n + off));
       }
     }
   } else {
@@ -812,8 +863,8 @@ __device__ __forceinline__ void lattice_tile_pair(const View &v, const S *__rest
       const int cx = L::cx(i);
       const S *row = fin + (v.soff[i] + n + ro[1 - L::cy(i)][1 - L::cz(i)]);
       e[i] = M(0);
-      if (cx > 0 && need_up) e[i] = Units<S>::template load<M>(__ldg(row - 1));
-      if (cx < 0 && need_dn) e[i] = Units<S>::template load<M>(__ldg(row + 2));
+      if (cx > 0 && need_up) e[i] = Units<S>::template load<M>(LD_POP(v, fin, row - 1));
+      if (cx < 0 && need_dn) e[i] = Units<S>::template load<M>(LD_POP(v, fin, row + 2));
     }
   }
   M f0[L::Q], f1[L::Q];
@@ -843,18 +894,18 @@ __device__ __forceinline__ void lattice_tile_pair(const View &v, const S *__rest
   if (fa && fb) {
 #pragma unroll
     for (int i = 0; i < L::Q; ++i)
-      *reinterpret_cast<T *>(fout + (v.soff[i] + n)) = V::make(pa[i], pb[i]);
+      ST_POP2(v, fout, fout + (v.soff[i] + n), V::make(pa[i], pb[i]));
   } else if (sa || sb) {
     const uint32_t ka = ga ? v.amask[n] : (fa ? 0u : ~0u), kb = gb ? v.amask[n + 1] : (fb ? 0u : ~0u);
     if (!(ka | kb)) {
 #pragma unroll
       for (int i = 0; i < L::Q; ++i)
-        *reinterpret_cast<T *>(fout + (v.soff[i] + n)) = V::make(pa[i], pb[i]);
+        ST_POP2(v, fout, fout + (v.soff[i] + n), V::make(pa[i], pb[i]));
     } else {
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) {
-        if (!((ka >> i) & 1u)) fout[(long long)i * np + n] = Units<S>::template store<M>(pa[i]);
-        if (!((kb >> i) & 1u)) fout[(long long)i * np + n + 1] = Units<S>::template store<M>(pb[i]);
+        if (!((ka >> i) & 1u)) ST_POP(v, fout, &fout[(long long)i * np + n], Units<S>::template store<M>(pa[i]));
+        if (!((kb >> i) & 1u)) ST_POP(v, fout, &fout[(long long)i * np + n + 1], Units<S>::template store<M>(pb[i]));
       }
     }
   }
@@ -1000,7 +1051,13 @@ __device__ void tma_issue(const View &v, const S *__restrict__ fin, int2 tile, u
       zs = zs < 0 ? zs + v.nz : (zs >= v.nz ? zs - v.nz : zs);
       int ys = y0 + h - dcy<L>(i);
       ys = ys < 0 ? ys + v.ny : (ys >= v.ny ? ys - v.ny : ys);
-      const S *src = fin + (long long)i * v.np + zs * plane + (long long)ys * v.nxp + xa;
+      long long first = (long long)i * v.np + zs * plane + (long long)ys * v.nxp + xa;
+      // a range outside the buffer is recorded, and the copy then reads the
+      // buffer's start instead, so that the stage's byte count still completes
+      if (!pop_index_ok(v, first, __LINE__) ||
+          !pop_index_ok(v, first + rowbytes / (uint32_t)sizeof(S) - 1, __LINE__))
+        first = 0;
+      const S *src = fin + first;
       S *dst = pops + ((long long)i * H + h) * lay.rowlen + (xa - (x0 - HALO));
       bulk_g2s(dst, src, rowbytes, bar);
     }
@@ -1047,13 +1104,13 @@ __device__ __forceinline__ void tma_lattice(const View &v, const S *__restrict__
 #pragma unroll
     for (int i = 0; i < L::Q; ++i)
       f[i] = L::cx(i) == 0 ? Units<S>::template load<M>(pops[(i * lay.H + ty) * lay.rowlen + tx + HALO])
-                           : Units<S>::template load<M>(__ldg(fin + (long long)i * v.np + n +
-                                                              nb.at(-L::cx(i), -L::cy(i), -L::cz(i))));
+                           : Units<S>::template load<M>(LD_POP(v, fin, fin + (long long)i * v.np + n +
+                                                                  nb.at(-L::cx(i), -L::cy(i), -L::cz(i))));
   }
   if (here && v.bc == BC_BFL && (fl & F_BOUNDARY)) bfl_complete<L, M>(v, *record_of(v, n, bal), f);
   const Macro<L, M> m = moments<L, M, Units<S>::kStored>(v, f);
-  if (masked) collide_store<L, S, M, PHYS>(v, f, m, fout + n, np, skip);
-  else collide_store<L, S, M, PHYS>(v, f, m, fout + n, np, 0u);
+  if (masked) collide_store<L, S, M, PHYS>(v, f, m, fout, n, np, skip);
+  else collide_store<L, S, M, PHYS>(v, f, m, fout, n, np, 0u);
 }
 
 template <class L, typename S, typename M, int PHYS>
@@ -1145,19 +1202,23 @@ __global__ void __launch_bounds__(256, MINB) k_step_batch(const BatchEntry *__re
   __shared__ M stage[L::Q * stage_threads<L, M>()];
   __shared__ BatchEntry se;
   const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  int held = -1;  // the entry in se; a block's tiles mostly belong to one simulation
   for (int k = 0; k < T; ++k) {
     const int idx = blockIdx.x * T + k;
     if (idx >= ntiles) break;  // uniform across the block
     const int4 tile = tiles[idx];
-    __syncthreads();  // the previous tile is done with se
-    {  // the first warp copies the entry in 16-byte pieces
-      constexpr int kPieces = (int)(sizeof(BatchEntry) / 16);
-      const int4 *src = reinterpret_cast<const int4 *>(entries + tile.x);
-      int4 *dst = reinterpret_cast<int4 *>(&se);
-      if (t < 32)
-        for (int k = t; k < kPieces; k += 32) dst[k] = __ldg(src + k);
+    if (tile.x != held) {  // uniform across the block
+      __syncthreads();  // the previous tile is done with se
+      {  // the first warp copies the entry in 16-byte pieces
+        constexpr int kPieces = (int)(sizeof(BatchEntry) / 16);
+        const int4 *src = reinterpret_cast<const int4 *>(entries + tile.x);
+        int4 *dst = reinterpret_cast<int4 *>(&se);
+        if (t < 32)
+          for (int k = t; k < kPieces; k += 32) dst[k] = __ldg(src + k);
+      }
+      __syncthreads();
+      held = tile.x;
     }
-    __syncthreads();
     const S *fin = static_cast<const S *>(parity ? se.f1 : se.f0);
     S *fout = static_cast<S *>(parity ? const_cast<void *>(se.f0) : se.f1);
     // each simulation takes the same compiled path as when it steps alone: the
@@ -1189,7 +1250,7 @@ __global__ void k_init(const View v, S *__restrict__ fout, double rho, double ux
   if ((fl & F_BOUNDARY) && v.bc == BC_BFL) bfl_encode<L, M>(v, *record_of(v, n, bal), f);
 #pragma unroll
   for (int i = 0; i < L::Q; ++i)
-    fout[(long long)i * v.np + n + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))] = to_store<S, M>(f[i]);
+    ST_POP(v, fout, &fout[(long long)i * v.np + n + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))], to_store<S, M>(f[i]));
 }
 
 // Host-layout FP64 populations fh[(x + nx*(y + ny*z))*Q + i] -> slots (unshifted in, shifted stored).
@@ -1212,7 +1273,7 @@ __global__ void k_set_pop(const View v, S *__restrict__ fout, const double *__re
   if ((fl & F_BOUNDARY) && v.bc == BC_BFL) bfl_encode<L, M>(v, *record_of(v, n, bal), f);
 #pragma unroll
   for (int i = 0; i < L::Q; ++i)
-    fout[(long long)i * v.np + n + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))] = to_store<S, M>(f[i]);
+    ST_POP(v, fout, &fout[(long long)i * v.np + n + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))], to_store<S, M>(f[i]));
 }
 
 // Pre-collision populations (gathered, BFL-completed), macroscopic fields, and the
@@ -1328,9 +1389,9 @@ __global__ void __launch_bounds__(256) k_force(const View v, const S *__restrict
       const int ib = opp<L>(i);
       const double w = weight<L>(i);
       const M fpost_m = (r.shell & bit) ? (prev ? post_r<L, M>(v, P, ib, fp[ib], fp[i], mp) : M(0))
-                                        : to_math<S, M>(cur[(long long)ib * v.np + n]);
+                                        : to_math<S, M>(LD_POP(v, cur, &cur[(long long)ib * v.np + n]));
       const double fpost_ib = (double)fpost_m + w * v.rho0;
-      double fnew = (double)to_math<S, M>(cur[(long long)i * v.np + n + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))]);
+      double fnew = (double)to_math<S, M>(LD_POP(v, cur, &cur[(long long)i * v.np + n + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))]));
       if (v.bc == BC_BFL && (r.ffok & bit)) {
         const M q = lq[li];
         if (q < M(0.5))

@@ -210,6 +210,8 @@ struct View {
   const int *dyn_count;      // device: number of records in dyn (null: no moving body)
   int *err;                  // device error word (bounded waits that ran out set bit 0)
   long long wait_limit;      // polls before a first wait of the TMA-staged step counts as hung
+  unsigned long long *dbg;   // LBM_DEBUG builds: first out-of-range population index (kernels.cuh LD_POP)
+  long long dbg_limit;       // LBM_DEBUG builds: population indices at or above it count as out of range
 
   __host__ __device__ RecSet stat() const { return RecSet{rec, rnode, lq, luw, luw1, ltag}; }
   const void *lq;            // [nl] q of each wall link (math type)

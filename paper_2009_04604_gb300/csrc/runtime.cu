@@ -110,6 +110,8 @@ extern "C" int lbm_create(int lattice, const int dims[3], double tau, int dtype,
   if (e == cudaSuccess) e = cudaMalloc(&h->dres, 8 * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&h->err_dev, sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess) e = cudaMalloc(&h->dbg_dev, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->dbg_dev, 0, sizeof(unsigned long long), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->flags, K_PAD, np, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->f[0], 0, bytes, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->f[1], 0, bytes, h->stream);
@@ -183,7 +185,7 @@ extern "C" int lbm_destroy(lbm_handle h) {
   h->drop_graphs();
   h->free_geometry();
   cudaFree(h->f[0]); cudaFree(h->f[1]); cudaFree(h->flags); cudaFree(h->cbase);
-  cudaFree(h->dres); cudaFree(h->scratch); cudaFree(h->tiles); cudaFree(h->err_dev);
+  cudaFree(h->dres); cudaFree(h->scratch); cudaFree(h->tiles); cudaFree(h->err_dev); cudaFree(h->dbg_dev);
   cudaFree(h->amask); cudaFree(h->stage_f);
   h->free_moving_body();
   if (h->own_stream) cudaStreamDestroy(h->stream);
@@ -204,6 +206,18 @@ extern "C" int lbm_synchronize(lbm_handle h) {
     cudaMemset(h->err_dev, 0, sizeof(int));
     return lbm_fail(h, LBM_ERR_TIMEOUT, "a bounded wait in the step kernel ran out; the step is incomplete");
   }
+#ifdef LBM_DEBUG
+  unsigned long long word = 0;
+  LBM_CUDA(h, cudaMemcpy(&word, h->dbg_dev, sizeof(word), cudaMemcpyDeviceToHost));
+  if (word) {
+    cudaMemset(h->dbg_dev, 0, sizeof(word));
+    char msg[160];
+    std::snprintf(msg, sizeof msg,
+                  "population index %lld (mod 2^40) out of range [0, %lld) at kernels.cuh line %llu; not accessed",
+                  (long long)(word & ((1ull << 40) - 1ull)), h->view().dbg_limit, word >> 40);
+    return lbm_fail(h, LBM_ERR_BOUNDS, msg);
+  }
+#endif
   return LBM_OK;
 }
 
@@ -299,6 +313,8 @@ View lbm_sim::view() const {
   v.flags = flags; v.amask = amask; v.cbase = cbase; v.rec = rec; v.rnode = rnode; v.nb = nb;
   v.err = err_dev;
   v.wait_limit = wait_limit;
+  v.dbg = dbg_dev;
+  v.dbg_limit = dbg_limit >= 0 ? dbg_limit : (long long)Q * np;
   v.tiles = tiles; v.gx = nxp / (step_bx * npt());
   invariant_divisor(v.gx, &v.gx_m, &v.gx_s);
   invariant_divisor(nxp, &v.nxp_m, &v.nxp_s);
@@ -852,6 +868,26 @@ extern "C" int lbm_load(lbm_handle h, const void *buf, size_t bytes) {
   }
   h->state_ok = true;
   return LBM_OK;
+}
+
+extern "C" int lbm_is_debug_build(void) {
+#ifdef LBM_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+extern "C" int lbm_set_debug_limit(lbm_handle h, long long elements) {
+  if (!h) return lbm_fail(nullptr, LBM_ERR_ARG, "null handle");
+#ifdef LBM_DEBUG
+  h->dbg_limit = elements < 0 ? -1 : elements;
+  h->drop_graphs();
+  return LBM_OK;
+#else
+  (void)elements;
+  return lbm_fail(h, LBM_ERR_STATE, "not a debug build (compile with LBM_DEBUG)");
+#endif
 }
 
 extern "C" int lbm_set_wait_limit(lbm_handle h, long long polls) {

@@ -79,6 +79,8 @@ struct lbm_sim {
 
   double *dres = nullptr;     // reduction results (device)
   int *err_dev = nullptr;     // device error word (bit 0: a bounded wait ran out)
+  unsigned long long *dbg_dev = nullptr;  // LBM_DEBUG builds: first out-of-range population index
+  long long dbg_limit = -1;   // LBM_DEBUG builds: index limit of the checks (-1: Q x padded nodes)
   double *scratch = nullptr;  // per-block reduction partials (device)
   long long scratch_len = 0;
   double *stage_f = nullptr;  // FP64 staging of lbm_set/get_populations (N*Q, device; kept)

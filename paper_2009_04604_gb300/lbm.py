@@ -15,7 +15,10 @@ import re
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
+# LBM_LIBRARY selects another build of the library, e.g. the bounds-checked one
+# (build.build(debug=True) writes _build_debug/liblbm.so)
+LIB_PATH = os.environ.get("LBM_LIBRARY") or os.path.join(_HERE, "_build", "liblbm.so")
+DEBUG_LIB_PATH = os.path.join(_HERE, "_build_debug", "liblbm.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "lbm.h")
 
 D2Q9, D3Q19, D3Q27 = 0, 1, 2
@@ -31,7 +34,7 @@ BCS = {"elibb_f": BC_ELIBB_F, "elibb_fq": BC_ELIBB_FQ, "bfl": BC_BFL, "hwbb": BC
        "elibb_u": BC_ELIBB_U, "elibb_uq": BC_ELIBB_UQ}
 COLLISIONS = {"bgk": COLL_BGK, "trt": COLL_TRT}
 STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_OOM",
-          -4: "LBM_ERR_NONFINITE", -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_STATE"}
+          -4: "LBM_ERR_NONFINITE", -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_STATE", -7: "LBM_ERR_BOUNDS"}
 
 
 class LBMError(RuntimeError):
@@ -80,6 +83,8 @@ _SIGS = {
     "lbm_save": [ctypes.c_void_p, ctypes.c_void_p, P(ctypes.c_size_t)],
     "lbm_load": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
     "lbm_set_wait_limit": [ctypes.c_void_p, ctypes.c_longlong],
+    "lbm_set_debug_limit": [ctypes.c_void_p, ctypes.c_longlong],
+    "lbm_is_debug_build": [],
     "lbm_set_moving_body": [ctypes.c_void_p, P(Shape), _d, ctypes.c_int, ctypes.c_int],
     "lbm_set_free_body": [ctypes.c_void_p, P(Shape), ctypes.c_double, ctypes.c_int],
     "lbm_get_body_history": [ctypes.c_void_p, _d, _i64],
@@ -116,6 +121,11 @@ def load():
         lib.lbm_batch_last_error.restype = ctypes.c_char_p
         _lib = lib
     return _lib
+
+
+def is_debug_build():
+    """Whether the loaded library checks population indices (LBM_DEBUG)."""
+    return bool(load().lbm_is_debug_build())
 
 
 def _check(rc, h=None):
@@ -339,6 +349,11 @@ class Simulation:
     def set_wait_limit(self, polls):
         """Testing aid: poll limit of the TMA-staged step's first waits (negative: default)."""
         self._ok(self.lib.lbm_set_wait_limit(self.h, int(polls)))
+
+    def set_debug_limit(self, elements):
+        """Bounds-checked builds: population indices at or above `elements` count as
+        out of range (negative: the buffer's size); see lbm_set_debug_limit."""
+        self._ok(self.lib.lbm_set_debug_limit(self.h, int(elements)))
 
     def set_launch(self, bx, by, variant=0, tiles=4):
         self._ok(self.lib.lbm_set_launch(self.h, int(bx), int(by), int(variant), int(tiles)))

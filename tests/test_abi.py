@@ -64,6 +64,9 @@ def test_host_argument_errors(lib):
     assert lib.lbm_create(lbm.D3Q19, dims, 0.8, lbm.F32, None, None) == -1
     assert lib.lbm_step(None, 1) == -1
     assert lib.lbm_lattice_info(5, None, None, None) == -1
+    # the default build does not check population indices (LBM_DEBUG)
+    assert lib.lbm_is_debug_build() == 0
+    assert lib.lbm_set_debug_limit(None, 5) == -1
 
 
 def test_oracle_and_library_share_no_code():
