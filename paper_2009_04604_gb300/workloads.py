@@ -77,6 +77,32 @@ def shear_channel_ellipse(nx=128, ny=98, U=0.04, tau=0.8, ra=8.0, rb=4.0, ang0=0
                 inertia=math.pi * ra * rb * (ra * ra + rb * rb) / 4.0, gamma=U / H, U=U, aspect=ra / rb)
 
 
+def shear_channel_spheroid(nx=96, ny=74, nz=40, U=0.04, tau=0.8, ra=8.0, rb=4.0, ang0=0.0):
+    """D3Q19 shear channel for the 3-D Jeffery's orbit (Sec. III.C): walls at
+    y = 0 and y = ny-1 moving at -U/2 and +U/2 (H = ny - 2), periodic in x and z,
+    the linear shear flow as the initial state, and a prolate spheroid at the
+    centre with semi-axis ra along its body y axis (vertical at ang0 = 0) and rb
+    along its body x and z axes. With its axis in the flow-gradient plane the
+    spheroid turns about z only. Its moment of inertia about z is the solid
+    spheroid's at density 1, m (ra^2 + rb^2) / 5 with m = 4/3 pi ra rb^2."""
+    H = ny - 2
+    N = nx * ny * nz
+    y = (np.arange(N) // nx) % ny
+    base = np.zeros(N, np.uint8)
+    base[(y == 0) | (y == ny - 1)] = SOLID
+    base_u = np.zeros((N, 3))
+    base_u[y == 0, 0] = -0.5 * U
+    base_u[y == ny - 1, 0] = 0.5 * U
+    u0 = np.zeros((N, 3))
+    u0[:, 0] = -0.5 * U + U * (y - 0.5) / H
+    centre = (nx / 2.0 - 0.3, (ny - 1) / 2.0, nz / 2.0 + 0.2)
+    body = dict(type="ellipsoid", tag=1, c=centre, r=(rb, ra, rb), ang=ang0)
+    mass = 4.0 / 3.0 * math.pi * ra * rb * rb
+    return dict(lattice=D3Q19, dims=(nx, ny, nz), tau=tau, xshift=0, force=(0.0, 0.0, 0.0), rho0=1.0,
+                base=base, base_u=base_u, shapes=[], u0=u0, body=body,
+                inertia=mass * (ra * ra + rb * rb) / 5.0, gamma=U / H, U=U, aspect=ra / rb)
+
+
 def duct_base(dims, u_in):
     """Base node kinds of a duct along x: side walls at y, z = 0 and n-1; inlet plane
     x = 0 (a wall moving with u_in, half-way from the first fluid layer); open
