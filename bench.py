@@ -524,9 +524,18 @@ def ours_arm(args, rank, world, dist):
         try:
             import oracle
             oracle.build()
+            threads = oracle.set_threads(0)
             mlups_cpu, steps_cpu, dt_cpu, _ = run_oracle(wl, 15.0, min_steps=2)
-            cpu = {"value": round(mlups_cpu, 4), "unit": "MLUPS", "cores": cores_used(), "kind": "oracle",
-                   "sample": f"{steps_cpu} full-size steps of {WORKLOAD} in {dt_cpu:.1f} s (FP64 oracle, OpenMP)"}
+            cpu = {"value": round(mlups_cpu, 4), "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                   "sample": f"{steps_cpu} full-size steps of {WORKLOAD} in {dt_cpu:.1f} s (FP64 oracle, "
+                             f"OpenMP, {threads} threads)"}
+            # the same oracle on one core, on the 64x32x32 downscale (about 5 s)
+            oracle.set_threads(1)
+            small = W.sphere_duct_small()
+            m1, st1, dt1, _ = run_oracle(small, 5.0, min_steps=2)
+            oracle.set_threads(threads)
+            cpu["single_thread"] = {"value": round(m1, 4), "unit": "MLUPS", "cores": 1,
+                                    "sample": f"{st1} steps of the 64x32x32 duct downscale in {dt1:.1f} s"}
         except Exception as exc:
             cpu = {"value": None, "unit": "MLUPS", "cores": cores_used(), "kind": "oracle", "error": str(exc)[:200]}
     _, u = s.macros()

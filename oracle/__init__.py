@@ -233,6 +233,14 @@ def geometry(p, base=None, base_u=None, shapes=(), with_shell=False):
     return flags, q, uw, uw1, tag
 
 
+def set_threads(n=0):
+    """OpenMP threads of the oracle's loops (n <= 0 keeps the setting); returns
+    the number in use."""
+    lib = _load()
+    lib.or_set_threads.restype = ctypes.c_int
+    return int(lib.or_set_threads(int(n)))
+
+
 def torque(p, q, tag, flink, centre, want_tag=-1):
     """Torque about ``centre`` of the link forces ``flink`` (from ``step``) of the
     links with tag ``want_tag`` (-1: all): sum (x_W - c) x F, x_W = x_F - q c_i."""

@@ -49,6 +49,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define QMAX 27
 
@@ -741,4 +744,16 @@ void or_torque(const or_params *p, const double *q, const int32_t *tag, const do
       T[2] += r[0] * F[1] - r[1] * F[0];
     }
   }
+}
+
+/* ---- threads ---- */
+
+int or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }

@@ -152,6 +152,11 @@ long or_geometry(const or_params *p, const uint8_t *base, const double *base_u,
  * links with the given tag (tag < 0: every wall link): T = sum (x_W - c) x F_link,
  * with x_W = x_F - q c_i the link's wall point (Sec. II.F; the moment of the
  * link forces of Eq. force-boundary-node). q and tag as or_geometry writes them. */
+/* Number of OpenMP threads of the oracle's loops (n <= 0 keeps the current
+ * setting); returns the number in use (1 without OpenMP). Used to time the
+ * oracle on one core. */
+int or_set_threads(int n);
+
 void or_torque(const or_params *p, const double *q, const int32_t *tag, const double *flink, int want_tag,
                const double c[3], double T[3]);
 

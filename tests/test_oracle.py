@@ -583,3 +583,25 @@ def test_inclined_channel_reaches_the_steady_parabola():
     uth = wl["g"] / (2.0 * nu) * s * (40.0 - s)
     assert A.rrse(u[fl] @ np.array(wl["channel_dir"]), uth) < 1e-3
     assert np.abs(u[fl] @ np.array(wl["channel_nrm"])).max() < 1e-3 * uth.max()
+
+
+def test_thread_count_leaves_the_update_unchanged(oracle_lib):
+    """The oracle's OpenMP loops write each node's populations independently
+    (Eq. 1-2 are local after streaming), so one thread and all threads give the
+    same bits; the CPU baseline times both."""
+    wl = W.sphere_duct_small()
+    kinds = {"sphere": oracle.SHAPE_SPHERE}
+    shapes = [dict(s, type=kinds[s["type"]]) for s in wl["shapes"]]
+    p = oracle.params(wl["lattice"], wl["dims"], wl["tau"], bc=oracle.BC_ELIBB_F, rho0=wl["rho0"],
+                      force=wl["force"], xshift=wl["xshift"])
+    flags, q, uw, uw1, _ = oracle.geometry(p, wl["base"], wl["base_u"], shapes)
+    f0 = oracle.init_eq(p, flags)
+    threads = oracle.set_threads(0)
+    try:
+        assert oracle.set_threads(1) == 1
+        a, fa = oracle.step(p, flags, f0, q, uw, uw1, want_force=True)
+        oracle.set_threads(max(threads, 2))
+        b, fb = oracle.step(p, flags, f0, q, uw, uw1, want_force=True)
+    finally:
+        oracle.set_threads(threads)
+    assert np.array_equal(a, b) and np.array_equal(fa, fb)
