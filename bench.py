@@ -395,10 +395,10 @@ def accuracy_duct(lbm, W, dtype, tuned):
             "launch": list(launch)}
 
 
-def accuracy_porous(lbm, W, dtype):
+def accuracy_porous(lbm, W, dtype, tuned):
     """Velocity error of the porous-medium downscale with the moving sphere at the
     configured body force g = 1e-6 (48^3, 1500 steps) against the oracle's run
-    stored by tests/golden/make_porous_reference.py."""
+    stored by tests/golden/make_porous_reference.py, at the timed launch."""
     ref = np.load(os.path.join(GOLDEN, "porous_48_g1e-6_t1500.npz"))
     wl = W.porous_with_moving_sphere(n=48, rmin=3.0, rmax=5.0, moving_radius=4.0, amplitude=3.0,
                                      period=300, seed=5, g=1e-6)
@@ -406,6 +406,8 @@ def accuracy_porous(lbm, W, dtype):
     s.set_options("elibb_f", 1.0, wl["force"], 0)
     s.build_geometry(None, None, wl["shapes"])
     s.set_moving_body(wl["body"], wl["traj"], 0)
+    launch = clip_launch(tuned, 64)
+    s.set_launch(*launch)
     s.init(1.0)
     s.step(int(ref["steps"]))
     flags = s.get_geometry()[0]
@@ -413,7 +415,7 @@ def accuracy_porous(lbm, W, dtype):
     err = rel_l2(u.cpu().numpy()[flags == 0], ref["u"].astype(np.float64))
     s.close()
     return {"workload": "porous_48_moving_sphere_g1e-6", "steps": int(ref["steps"]),
-            "velocity_rel_l2_vs_oracle": float(f"{err:.3e}")}
+            "velocity_rel_l2_vs_oracle": float(f"{err:.3e}"), "launch": list(launch)}
 
 
 # ---------------------------------------------------------------- arms
@@ -559,7 +561,8 @@ def ours_arm(args, rank, world, dist):
         for dt in ("f32", "f16"):
             try:
                 extras["porous_moving_" + dt] = porous_moving(torch, lbm, W, dt, 100, peak)
-                extras["porous_moving_" + dt]["accuracy"] = accuracy["porous_" + dt] = accuracy_porous(lbm, W, dt)
+                extras["porous_moving_" + dt]["accuracy"] = accuracy["porous_" + dt] = accuracy_porous(
+                    lbm, W, dt, extras["porous_moving_" + dt]["launch"])
             except Exception as exc:
                 extras["porous_moving_" + dt] = {"error": str(exc)[:200]}
         for regime, st_ in (("large", 100), ("small", 400)):
