@@ -360,7 +360,7 @@ def clip_launch(tuned, nxp):
     """The timed launch, with the block narrowed (same threads per block) where a
     downscaled lattice's rows are too short for it."""
     bx, by, var, tiles = tuned["bx"], tuned["by"], tuned["variant"], tuned["tiles"]
-    per = 2 if var >= 5 else 1
+    per = 2 if 5 <= var <= 8 else 1
     while bx > 32 and nxp % (bx * per):
         bx //= 2
         by *= 2

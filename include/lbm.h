@@ -373,9 +373,18 @@ int lbm_set_debug_limit(lbm_handle h, long long elements);
  *     (switching to BFL moves the launch back to variant 0);
  *   variant 8: as 5..7, for blocks of exactly 128 threads, at least 7 resident
  *     per SM (72 registers a thread);
+ *   variant 9, 10: the split step. The lattice tiles and the boundary-record
+ *     tiles run as two kernels side by side in each step: the boundary kernel
+ *     on a second stream of the handle (highest priority), forked from and
+ *     joined back into the handle's stream around every step, so that nothing
+ *     after the step starts before both finish. The lattice kernel keeps at
+ *     least 6 (variant 9: 40 registers a thread) or 5 (variant 10: 48) resident
+ *     256-thread blocks per SM, the boundary kernel at least 4. One node per
+ *     thread; FP32/FP16/BF16. The results are those of variants 0..3;
  *   tiles 1..4: consecutive entries of the step kernel's tile table that one
  *     block processes. The table lists, plane by plane, the lattice tiles and
- *     then the boundary-record tiles.
+ *     then the boundary-record tiles (variants 9, 10: the lattice tiles; each
+ *     block of the boundary kernel takes one boundary-record tile).
  * FP64 storage accepts variant 0 only, and on D3Q27 at most 128 threads per block
  * (27 x 256 doubles of boundary staging would exceed the static shared memory).
  * The default is the widest bx <= 128 that divides the row, by = 256/bx (128/bx

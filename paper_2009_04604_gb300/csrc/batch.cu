@@ -135,10 +135,12 @@ static int build_batch(lbm_batch b) {
     const int c = (s->has_force ? PH_FORCE : 0) | (s->collision == LBM_COLL_TRT ? PH_TRT : 0);
     if (b->cls_count[c] == 0) b->cls_first[c] = (long long)t.size();
     const size_t t0 = t.size();
-    const int save_bx = s->step_bx;
-    s->step_bx = b->bx;  // the view's tile-row count follows the batch's block width
+    const int save_bx = s->step_bx, save_var = s->variant;
+    s->step_bx = b->bx;        // the view's tile-row count follows the batch's block width
+    s->variant = b->variant;   // and its one-node lattice tiles (a simulation may be set to node pairs)
     e[k].v = s->view();
     s->step_bx = save_bx;
+    s->variant = save_var;
     e[k].v.tiles = nullptr;
     e[k].f0 = s->f[s->cur];
     e[k].f1 = s->f[s->cur ^ 1];

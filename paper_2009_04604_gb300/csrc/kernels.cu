@@ -66,9 +66,9 @@ cudaError_t prepare_step_tma(int lattice, int dtype, int phys, int bx, int by, l
 }
 
 cudaError_t launch_step(int lattice, int dtype, int variant, const View &v, const void *fin,
-                        void *fout, const Launch &l) {
+                        void *fout, const Launch &l, const Launch *lb) {
   return dispatch(lattice, dtype, [&]<class L, typename S, typename M>() {
-    return launch_step_ls<L, S>(variant, v, fin, fout, l);
+    return launch_step_ls<L, S>(variant, v, fin, fout, l, lb);
   });
 }
 

@@ -956,6 +956,39 @@ __global__ void __launch_bounds__(MAXT, MINB) k_step(const View v, const S *__re
   }
 }
 
+// ---------------------------------------------------------------- split step
+// The same step as two kernels that run side by side (launch variants 9 and 10):
+// k_lattice takes the lattice tiles of the table v.tiles (no boundary entries),
+// k_boundary the boundary tiles of v.btiles, one entry per block. Both only read
+// fin and write disjoint slots of fout, so they need no ordering within a step;
+// the host forks the boundary kernel onto a second stream and joins it before
+// the next step. The point is the register budget: the boundary tiles' link
+// loop needs about 64 registers a thread, the lattice tiles alone 40 (no body
+// force) or 48 (with one) without spilling, so the lattice kernel keeps 48 or
+// 40 warps per SM resident instead of the combined kernel's 32.
+template <class L, typename S, typename M, int MINB, int PHYS>
+__global__ void __launch_bounds__(256, MINB) k_lattice(const View v, const S *__restrict__ fin,
+                                                       S *__restrict__ fout) {
+  const int T = v.tpb_tiles;
+  const int first = blockIdx.x * T;
+  int2 tl[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (k < T && first + k < v.ntiles) tl[k] = v.tiles[first + k];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (k >= T || first + k >= v.ntiles) break;
+    lattice_tile<L, S, M, PHYS>(v, fin, fout, tl[k]);
+  }
+}
+
+template <class L, typename S, typename M>
+__global__ void __launch_bounds__(256, 4) k_boundary(const View v, const S *__restrict__ fin,
+                                                     S *__restrict__ fout) {
+  __shared__ M stage[L::Q * stage_threads<L, M>()];  // populations, [direction][thread]
+  boundary_tile<L, S, M>(v, fin, fout, v.btiles[blockIdx.x], stage);
+}
+
 // ---------------------------------------------------------------- TMA-staged step
 // A persistent variant of k_step for FP32/FP16/BF16 storage. Each block walks
 // the tile table with a grid stride. For a lattice tile, one producer thread

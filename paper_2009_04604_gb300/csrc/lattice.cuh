@@ -205,6 +205,7 @@ struct View {
   // c_iy nxp + c_iz nxp ny) (the source of population i at an interior node)
   int soff[27], loff[27];
   int ntiles, tpb_tiles;     // table length; consecutive table entries per block
+  const int2 *btiles;        // split step (variants 9, 10): the boundary entries, apart from v.tiles
   // moving body: records of the nodes of its region, rebuilt every step
   RecSet dyn;
   const int *dyn_count;      // device: number of records in dyn (null: no moving body)

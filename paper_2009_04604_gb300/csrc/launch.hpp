@@ -23,11 +23,13 @@ cudaError_t prepare_step_tma(int lattice, int dtype, int phys, int bx, int by, l
 
 // lattice: 0 D2Q9, 1 D3Q19, 2 D3Q27; dtype: 0 F64, 1 F32, 2 F16, 3 BF16
 // variant: register budget of the step kernel, at least variant+1 resident
-// 256-thread blocks per SM (0..3), 4: the TMA-staged persistent kernel, or 5..7:
-// two nodes per thread with at least 1..3 resident blocks per SM (FP32/FP16/BF16).
-// FP64 has a single variant.
+// 256-thread blocks per SM (0..3), 4: the TMA-staged persistent kernel, 5..7:
+// two nodes per thread with at least 1..3 resident blocks per SM, 8: two nodes
+// per thread in 128-thread blocks, 9 and 10: the split step, whose lattice kernel
+// keeps at least 6 or 5 resident 256-thread blocks per SM and whose boundary
+// kernel runs with the launch lb (FP32/FP16/BF16). FP64 has a single variant.
 cudaError_t launch_step(int lattice, int dtype, int variant, const View &v, const void *fin,
-                        void *fout, const Launch &l);
+                        void *fout, const Launch &l, const Launch *lb = nullptr);
 cudaError_t launch_init(int lattice, int dtype, const View &v, void *fout, double rho, double ux,
                         double uy, double uz, const Launch &l);
 cudaError_t launch_set_pop(int lattice, int dtype, const View &v, void *fout, const double *fh,

@@ -186,8 +186,12 @@ extern "C" int lbm_destroy(lbm_handle h) {
   h->free_geometry();
   cudaFree(h->f[0]); cudaFree(h->f[1]); cudaFree(h->flags); cudaFree(h->cbase);
   cudaFree(h->dres); cudaFree(h->scratch); cudaFree(h->tiles); cudaFree(h->err_dev); cudaFree(h->dbg_dev);
+  cudaFree(h->btiles);
   cudaFree(h->amask); cudaFree(h->stage_f);
   h->free_moving_body();
+  if (h->aux) { cudaStreamSynchronize(h->aux); cudaStreamDestroy(h->aux); }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
   return LBM_OK;
@@ -243,7 +247,7 @@ extern "C" int lbm_set_options(lbm_handle h, int bc, double rho0, const double f
     if (e != cudaSuccess) { h->bc = old_bc; return lbm_fail(h, LBM_ERR_CUDA, cudaGetErrorString(e)); }
   }
   h->bc = bc;
-  if (bc == LBM_BC_BFL && h->variant >= 5) { h->variant = 0; h->tune_default(); }  // pairs have no BFL path
+  if (bc == LBM_BC_BFL && h->npt() == 2) { h->variant = 0; h->tune_default(); }  // pairs have no BFL path
   h->rho0 = rho0;
   h->has_force = 0;
   for (int a = 0; a < 3; ++a) {
@@ -326,6 +330,7 @@ View lbm_sim::view() const {
     v.loff[i] = (int)((long long)i * np - (c[0] + (long long)c[1] * nxp + (long long)c[2] * nxp * ny));
   }
   v.ntiles = (int)ntiles; v.tpb_tiles = tiles_per_block;
+  v.btiles = btiles;
   if (mb.on) {
     v.dyn = RecSet{mb.rec[cur], mb.rnode[cur], mb.lq[cur], mb.luw[cur], mb.luw1[cur], mb.ltag[cur]};
     v.dyn_count = mb.count[cur];
@@ -369,7 +374,8 @@ Launch lbm_sim::step_shape() const {
 
 // Tile table of the step kernel for the current geometry and launch shape: for
 // each plane z, its lattice tiles {z, t} (t = tile in the plane), then its
-// boundary tiles {-1 - count, first record}.
+// boundary tiles {-1 - count, first record}. The split step keeps the boundary
+// tiles in a table of their own (btiles), in the same order.
 int lbm_sim::ensure_tiles() {
   if (tiles && tiles_bx == step_bx && tiles_by == step_by && tiles_var == variant) return LBM_OK;
   const int tpb = step_bx * step_by;
@@ -378,22 +384,38 @@ int lbm_sim::ensure_tiles() {
   if (nb > 0)
     LBM_CUDA(this, cudaMemcpyAsync(hc.data(), cbase, hc.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
   LBM_CUDA(this, cudaStreamSynchronize(stream));
-  std::vector<int2> t;
+  std::vector<int2> t, bt;
+  std::vector<int2> &bdst = split() ? bt : t;
   t.reserve((size_t)nz * gx * gy + nb / tpb + nz + 1);
   const long long pchunks = (long long)nxp * ny / 32;
   for (int z = 0; z < nz; ++z) {
     for (int k = 0; k < gx * gy; ++k) t.push_back(make_int2(z, k));
     if (nb == 0) continue;
     const long long r0 = hc[z * pchunks], r1 = hc[(z + 1) * pchunks];
-    for (long long r = r0; r < r1; r += tpb) t.push_back(make_int2(-1 - (int)std::min<long long>(tpb, r1 - r), (int)r));
+    for (long long r = r0; r < r1; r += tpb)
+      bdst.push_back(make_int2(-1 - (int)std::min<long long>(tpb, r1 - r), (int)r));
   }
   if (mb.on)  // the moving body's records: as many tiles as the region could need
-    for (long long r = 0; r < mb.cap_rec; r += tpb) t.push_back(make_int2(DYN_TILE, (int)r));
+    for (long long r = 0; r < mb.cap_rec; r += tpb) bdst.push_back(make_int2(DYN_TILE, (int)r));
   cudaFree(tiles);
   tiles = nullptr;
+  cudaFree(btiles);
+  btiles = nullptr;
   ntiles = (long long)t.size();
+  nbtiles = (long long)bt.size();
   LBM_CUDA(this, cudaMalloc(&tiles, ntiles * sizeof(int2)));
   LBM_CUDA(this, cudaMemcpyAsync(tiles, t.data(), ntiles * sizeof(int2), cudaMemcpyHostToDevice, stream));
+  if (nbtiles > 0) {
+    LBM_CUDA(this, cudaMalloc(&btiles, nbtiles * sizeof(int2)));
+    LBM_CUDA(this, cudaMemcpyAsync(btiles, bt.data(), nbtiles * sizeof(int2), cudaMemcpyHostToDevice, stream));
+    if (!aux) {  // highest priority: the boundary blocks start as soon as the step does
+      int lo = 0, hi = 0;
+      LBM_CUDA(this, cudaDeviceGetStreamPriorityRange(&lo, &hi));
+      LBM_CUDA(this, cudaStreamCreateWithPriority(&aux, cudaStreamNonBlocking, hi));
+      LBM_CUDA(this, cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+      LBM_CUDA(this, cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+    }
+  }
   LBM_CUDA(this, cudaStreamSynchronize(stream));
   tiles_bx = step_bx;
   tiles_by = step_by;
@@ -560,7 +582,21 @@ int lbm_sim::launch_steps(int n) {
     if (rc) return rc;
   }
   for (int k = 0; k < n; ++k) {
-    cudaError_t e = launch_step(lattice, dtype, variant, view(), f[cur], f[cur ^ 1], step_shape());
+    cudaError_t e;
+    if (split() && nbtiles > 0) {
+      // the boundary kernel forks onto aux and joins before anything after the step
+      Launch lb;
+      lb.grid = dim3((unsigned)nbtiles, 1, 1);
+      lb.block = dim3(step_bx, step_by, 1);
+      lb.stream = aux;
+      e = cudaEventRecord(ev_fork, stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, ev_fork, 0);
+      if (e == cudaSuccess) e = launch_step(lattice, dtype, variant, view(), f[cur], f[cur ^ 1], step_shape(), &lb);
+      if (e == cudaSuccess) e = cudaEventRecord(ev_join, aux);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ev_join, 0);
+    } else {
+      e = launch_step(lattice, dtype, variant, view(), f[cur], f[cur ^ 1], step_shape());
+    }
     if (e != cudaSuccess) return lbm_fail(this, LBM_ERR_CUDA, cudaGetErrorString(e));
     if (mb.on) {
       int rc = move_after_step(f[cur ^ 1], cur ^ 1);
@@ -703,11 +739,12 @@ int lbm_sim::download(HostGeometry &g) {
 // ---------------------------------------------------------------- launch configuration
 static bool valid_launch(const lbm_sim *h, int bx, int by, int variant, int tiles) {
   if (bx < 32 || bx % 32 || h->nxp % bx || by < 1 || bx * by > 256) return false;
-  if (variant < 0 || variant > 8 || tiles < 1 || tiles > 4) return false;
+  if (variant < 0 || variant > 10 || tiles < 1 || tiles > 4) return false;
   if (variant == 8 && bx * by != 128) return false;  // compiled for blocks of 128 threads
   if (h->dtype == LBM_F64 && variant != 0) return false;
   if (h->dtype == LBM_F64 && h->lattice == LBM_D3Q27 && bx * by > 128) return false;  // shared staging
-  if (variant >= 5 && (h->nxp % (2 * bx) || h->bc == LBM_BC_BFL)) return false;  // pairs: whole rows, no BFL
+  if (variant >= 5 && variant <= 8 && (h->nxp % (2 * bx) || h->bc == LBM_BC_BFL))
+    return false;  // pairs: whole rows, no BFL
   return true;
 }
 
@@ -743,7 +780,7 @@ extern "C" int lbm_autotune(lbm_handle h, int steps, int *bx, int *by, int *vari
   int best[4] = {save[0], save[1], save[2], save[3]};
   float best_ms = 1e30f;
   int rc = LBM_OK;
-  const int nvar = h->dtype == LBM_F64 ? 1 : 9;  // 4: TMA-staged persistent kernel; 5-8: node pairs
+  const int nvar = h->dtype == LBM_F64 ? 1 : 11;  // 4: TMA-staged persistent kernel; 5-8: node pairs; 9-10: split
   const int tile_opts[3] = {1, 2, 4};
   for (int threads = 128; threads <= 256 && rc == LBM_OK; threads *= 2)
     for (int bxx = 32; bxx <= threads && rc == LBM_OK; bxx *= 2) {

@@ -90,6 +90,10 @@ struct lbm_sim {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // captured step loops, by starting buffer
   int2 *tiles = nullptr;      // step-kernel tile table (device)
   long long ntiles = 0;
+  int2 *btiles = nullptr;     // split step (variants 9, 10): the boundary entries (device)
+  long long nbtiles = 0;
+  cudaStream_t aux = nullptr;                         // split step: the boundary kernel's stream
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;   // split step: orders aux around each step
   int tiles_bx = 0, tiles_by = 0;  // launch shape the table was built for (0: stale)
   int tiles_per_block = 4;          // consecutive table entries per step-kernel block (1..4)
   int tiles_var = -1;               // register variant the launch data was prepared for
@@ -100,7 +104,8 @@ struct lbm_sim {
   MovingBody mb;
   std::string err;
 
-  int npt() const { return variant >= 5 ? 2 : 1; }  // nodes per thread along x in lattice tiles
+  int npt() const { return variant >= 5 && variant <= 8 ? 2 : 1; }  // nodes per thread along x in lattice tiles
+  bool split() const { return variant == 9 || variant == 10; }      // lattice and boundary kernels apart
   size_t elem_size() const;
   size_t link_size() const;
   void lattice_c(int i, int &x, int &y, int &z) const;

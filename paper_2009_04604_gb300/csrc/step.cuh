@@ -31,6 +31,26 @@ cudaError_t step_variant(const View &v, const void *fin, void *fout, const Launc
   return cudaGetLastError();
 }
 
+// The split step (variants 9, 10): the boundary kernel on lb.stream, then the
+// lattice kernel on l.stream. The caller orders the two streams around the pair.
+template <class L, typename S, typename M, int MINB>
+cudaError_t split_variant(const View &v, const void *fin, void *fout, const Launch &l, const Launch *lb) {
+  const S *a = static_cast<const S *>(fin);
+  S *b = static_cast<S *>(fout);
+  if (lb != nullptr && lb->grid.x > 0) {
+    k_boundary<L, S, M><<<lb->grid, lb->block, 0, lb->stream>>>(v, a, b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  switch (phys_of(v)) {
+    case PH_FORCE: k_lattice<L, S, M, MINB, PH_FORCE><<<l.grid, l.block, 0, l.stream>>>(v, a, b); break;
+    case PH_TRT: k_lattice<L, S, M, MINB, PH_TRT><<<l.grid, l.block, 0, l.stream>>>(v, a, b); break;
+    case PH_FORCE | PH_TRT: k_lattice<L, S, M, MINB, PH_FORCE | PH_TRT><<<l.grid, l.block, 0, l.stream>>>(v, a, b); break;
+    default: k_lattice<L, S, M, MINB, 0><<<l.grid, l.block, 0, l.stream>>>(v, a, b); break;
+  }
+  return cudaGetLastError();
+}
+
 // Shared-memory bytes of one stage of the TMA-staged step: the rows of every
 // population plane with a 16-byte halo on each side, the flag rows, and at least
 // the boundary tiles' staging array.
@@ -91,11 +111,14 @@ template <typename S> struct MathOf { using T = float; };
 template <> struct MathOf<double> { using T = double; };
 
 template <class L, typename S>
-cudaError_t launch_step_ls(int variant, const View &v, const void *fin, void *fout, const Launch &l) {
+cudaError_t launch_step_ls(int variant, const View &v, const void *fin, void *fout, const Launch &l,
+                           const Launch *lb) {
   using M = typename MathOf<S>::T;
   if constexpr (sizeof(M) == 8) {
     return step_variant<L, S, M, 1>(v, fin, fout, l);  // FP64: one register budget
   } else {
+    if (variant == 9) return split_variant<L, S, M, 6>(v, fin, fout, l, lb);
+    if (variant == 10) return split_variant<L, S, M, 5>(v, fin, fout, l, lb);
     if (variant == 4) {
       switch (phys_of(v)) {
         case PH_FORCE: return tma_launch<L, S, M, PH_FORCE>(v, fin, fout, l);
@@ -139,7 +162,7 @@ cudaError_t prepare_step_tma_ls(int phys, int bx, int by, long long ntiles, int 
 
 #define LBM_STEP_DECLARE(Lat, Sto)                                                                  \
   extern template cudaError_t launch_step_ls<Lat, Sto>(int, const View &, const void *, void *,    \
-                                                       const Launch &);                           \
+                                                       const Launch &, const Launch *);           \
   extern template cudaError_t prepare_step_tma_ls<Lat, Sto>(int, int, int, long long, int *, int *);
 
 }  // namespace lbm

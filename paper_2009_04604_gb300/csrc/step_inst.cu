@@ -7,7 +7,7 @@
 #if defined(LBM_STEP_LATTICE) && defined(LBM_STEP_STORE)
 namespace lbm {
 template cudaError_t launch_step_ls<LBM_STEP_LATTICE, LBM_STEP_STORE>(int, const View &, const void *, void *,
-                                                                     const Launch &);
+                                                                     const Launch &, const Launch *);
 template cudaError_t prepare_step_tma_ls<LBM_STEP_LATTICE, LBM_STEP_STORE>(int, int, int, long long, int *,
                                                                           int *);
 }  // namespace lbm

@@ -10,9 +10,10 @@ velocity inlet u = 0.02, pressure outlet, side walls, a sphere of radius 5, BGK
 tau = 0.7, 300 steps from rest. FP64 storage (one launch variant) must match the
 oracle's populations within 1e-12 relative L2; the other storage types must keep
 the velocity within their bounds: 1e-5 (FP32), 1e-3 (FP16), 2e-2 (BF16,
-reported). The TMA-staged kernel (variant 4) and BFL (one node per thread:
-the BFL completion finds its record by a one-node-per-lane ballot) are checked
-the same way."""
+reported). The TMA-staged kernel (variant 4), the split step (variants 9 and
+10: lattice and boundary tiles as two kernels side by side) and BFL (one node
+per thread: the BFL completion finds its record by a one-node-per-lane ballot)
+are checked the same way."""
 import numpy as np
 import pytest
 
@@ -83,6 +84,12 @@ CASES = [
     (lbm.BC_ELIBB_F, lbm.F16, (32, 4, 3, 2)),
     (lbm.BC_ELIBB_FQ, lbm.F16, (32, 4, 3, 2)),
     (lbm.BC_ELIBB_F, lbm.BF16, (32, 4, 3, 2)),
+    (lbm.BC_ELIBB_F, lbm.F32, (32, 8, 9, 1)),
+    (lbm.BC_ELIBB_FQ, lbm.F32, (64, 4, 10, 2)),
+    (lbm.BC_ELIBB_F, lbm.F16, (32, 8, 9, 1)),
+    (lbm.BC_ELIBB_FQ, lbm.F16, (64, 4, 9, 2)),
+    (lbm.BC_ELIBB_F, lbm.BF16, (32, 8, 9, 1)),
+    (lbm.BC_BFL, lbm.F32, (32, 8, 9, 1)),
 ]
 
 
