@@ -270,6 +270,7 @@ def dtype_variant(torch, lbm, W, dtype, steps, peak):
            "best_of": 5, "ms_per_step": round(ms / steps, 5), "launch": tuned}
     out.update(roofline_of(nfluid, padded_nodes(wl["dims"]), nb, nwall, 19, dtype, False, ms / steps, peak))
     out["traffic"] = profiled_traffic(f"k_step_d3q19_{dtype}_sphere_duct")
+    out["kernel"] = step_kernels(tuned)
     return out
 
 
@@ -299,6 +300,7 @@ def porous_moving(torch, lbm, W, dtype, steps, peak):
            "roofline_note": "static geometry's bytes; the moving sphere's few links add under 0.1 %"}
     out.update(roofline_of(nfluid, padded_nodes(wl["dims"]), nb, nwall, 19, dtype, False, ms / steps, peak))
     out["traffic"] = profiled_traffic(f"k_step_d3q19_{dtype}_porous_moving")
+    out["kernel"] = step_kernels(tuned)
     return out
 
 
@@ -354,6 +356,17 @@ def batched_vs_plain(torch, lbm, W, regime, dtype, steps, peak):
 
 # ---------------------------------------------------------------- accuracy beside the throughput
 GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def is_split(tuned):
+    """Launch variants 9 and 10: the lattice and boundary tiles as two kernels side by side."""
+    return tuned.get("variant") in (9, 10)
+
+
+def step_kernels(tuned):
+    """The kernel(s) of one step at this launch; for the split step the duration is
+    that of the fork-joined pair."""
+    return "k_lattice + k_boundary<D3Q19> (side by side)" if is_split(tuned) else "k_step<D3Q19>"
 
 
 def clip_launch(tuned, nxp):
@@ -589,10 +602,10 @@ def ours_arm(args, rank, world, dist):
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "peak_source": peak_kind, "algorithmic_bytes_per_launch": int(abytes),
                      "implementation_bytes_per_launch": int(implementation_bytes(nb)),
-                     "kernel": "k_step<D3Q19>", "duration_us": round(ms_step * 1e3, 2)},
+                     "kernel": step_kernels(tuned), "duration_us": round(ms_step * 1e3, 2)},
         "clocks": clk.summary(),
         "e2e": e2e,
-        "gpu_launches": args.steps * REPLAYS,
+        "gpu_launches": args.steps * REPLAYS * (2 if is_split(tuned) and nb > 0 else 1),
         "cpu_baseline": cpu,
         "state_finite": finite,
         "accuracy": accuracy,
