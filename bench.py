@@ -269,7 +269,7 @@ def dtype_variant(torch, lbm, W, dtype, steps, peak):
     out = {"value": round(nfluid * steps / (ms * 1e-3) / 1e6, 2), "unit": "MLUPS", "steps": steps,
            "best_of": 5, "ms_per_step": round(ms / steps, 5), "launch": tuned}
     out.update(roofline_of(nfluid, padded_nodes(wl["dims"]), nb, nwall, 19, dtype, False, ms / steps, peak))
-    out["traffic"] = profiled_traffic(f"k_step_d3q19_{dtype}_sphere_duct")
+    out["traffic"] = profiled_traffic(profile_name(tuned, dtype, "sphere_duct"))
     out["kernel"] = step_kernels(tuned)
     return out
 
@@ -299,7 +299,7 @@ def porous_moving(torch, lbm, W, dtype, steps, peak):
            "finite": finite, "ms_per_step": round(ms / steps, 4), "launch": tuned,
            "roofline_note": "static geometry's bytes; the moving sphere's few links add under 0.1 %"}
     out.update(roofline_of(nfluid, padded_nodes(wl["dims"]), nb, nwall, 19, dtype, False, ms / steps, peak))
-    out["traffic"] = profiled_traffic(f"k_step_d3q19_{dtype}_porous_moving")
+    out["traffic"] = profiled_traffic(profile_name(tuned, dtype, "porous_moving"))
     out["kernel"] = step_kernels(tuned)
     return out
 
@@ -367,6 +367,11 @@ def step_kernels(tuned):
     """The kernel(s) of one step at this launch; for the split step the duration is
     that of the fork-joined pair."""
     return "k_lattice + k_boundary<D3Q19> (side by side)" if is_split(tuned) else "k_step<D3Q19>"
+
+
+def profile_name(tuned, dtype, workload):
+    """The committed ncu summary of the step kernel(s) at this launch, dtype and workload."""
+    return f"{'k_lattice_k_boundary' if is_split(tuned) else 'k_step'}_d3q19_{dtype}_{workload}"
 
 
 def clip_launch(tuned, nxp):
@@ -506,7 +511,7 @@ def ours_arm(args, rank, world, dist):
     ls = 8 if args.dtype == "f64" else 4
     abytes = algorithmic_bytes(nfluid, np_, nb, nwall, 19, s_bytes, ls, False)
     achieved = abytes / (ms_step * 1e-3) / 1e9
-    traffic = profiled_traffic(f"k_step_d3q19_{args.dtype}_sphere_duct")
+    traffic = profiled_traffic(profile_name(tuned, args.dtype, "sphere_duct"))
     # ---- end to end through the public API: upload the state from pinned host memory,
     # then per step lbm_step(1) and a synchronising read of the drag force (24 B)
     K2 = 1000
