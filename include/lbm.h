@@ -381,6 +381,8 @@ int lbm_set_debug_limit(lbm_handle h, long long elements);
  *     least 6 (variant 9: 40 registers a thread) or 5 (variant 10: 48) resident
  *     256-thread blocks per SM, the boundary kernel at least 4. One node per
  *     thread; FP32/FP16/BF16. The results are those of variants 0..3;
+ *   variant 11, 12: as 0..3, with at least 5 (48 registers a thread) or 6 (40)
+ *     resident 256-thread blocks per SM. FP32/FP16/BF16;
  *   tiles 1..4: consecutive entries of the step kernel's tile table that one
  *     block processes. The table lists, plane by plane, the lattice tiles and
  *     then the boundary-record tiles (variants 9, 10: the lattice tiles; each

@@ -591,6 +591,19 @@ __device__ __forceinline__ void boundary_rule(const View &v, const RecSet &rs, c
   }
 }
 
+// The general rule (TRT, the regularized wall estimate, BFL, HWBB, ELIBB-U/UQ) is a
+// call of its own: its registers then do not count against a step kernel's budget,
+// which the lattice tiles and the specialised rules set, and a kernel compiled for
+// 40 or 48 registers spills only around this call, on the general path. The step
+// kernels take their view as a grid constant, so that passing it by reference
+// makes no per-thread copy.
+template <class L, typename S, typename M>
+__device__ __noinline__ void boundary_general(const View &v, const RecSet &rs, const Rec &r, const M *fs,
+                                              int stride, const Macro<L, M> &m, const M (&pi)[6], long long n,
+                                              int x, int y, int z, S *__restrict__ fout) {
+  boundary_rule<L, S, M, -1>(v, rs, r, fs, stride, m, pi, n, x, y, z, fout);
+}
+
 template <class L, typename S, typename M>
 __device__ void boundary(const View &v, const RecSet &rs, const Rec &r, const M *fs, int stride,
                          const Macro<L, M> &m, const M (&pi)[6], long long n, int x, int y, int z,
@@ -601,7 +614,7 @@ __device__ void boundary(const View &v, const RecSet &rs, const Rec &r, const M 
   else if (bgk_bb && v.bc == BC_ELIBB_FQ)
     boundary_rule<L, S, M, BC_ELIBB_FQ>(v, rs, r, fs, stride, m, pi, n, x, y, z, fout);
   else
-    boundary_rule<L, S, M, -1>(v, rs, r, fs, stride, m, pi, n, x, y, z, fout);
+    boundary_general<L, S, M>(v, rs, r, fs, stride, m, pi, n, x, y, z, fout);
 }
 
 // non-binding request to bring the line holding p into L1
@@ -938,7 +951,7 @@ __device__ __forceinline__ void boundary_tile(const View &v, const S *__restrict
 // descriptors it loads together up front. MAXT: the largest block the register
 // budget is set for (MINB resident blocks of MAXT threads).
 template <class L, typename S, typename M, int MINB, int PHYS, bool PAIR = false, int MAXT = 256>
-__global__ void __launch_bounds__(MAXT, MINB) k_step(const View v, const S *__restrict__ fin,
+__global__ void __launch_bounds__(MAXT, MINB) k_step(const __grid_constant__ View v, const S *__restrict__ fin,
                                                      S *__restrict__ fout) {
   __shared__ M stage[L::Q * stage_threads<L, M>()];  // boundary tiles: populations, [direction][thread]
   const int T = v.tpb_tiles;
@@ -967,7 +980,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_step(const View v, const S *__re
 // force) or 48 (with one) without spilling, so the lattice kernel keeps 48 or
 // 40 warps per SM resident instead of the combined kernel's 32.
 template <class L, typename S, typename M, int MINB, int PHYS>
-__global__ void __launch_bounds__(256, MINB) k_lattice(const View v, const S *__restrict__ fin,
+__global__ void __launch_bounds__(256, MINB) k_lattice(const __grid_constant__ View v, const S *__restrict__ fin,
                                                        S *__restrict__ fout) {
   const int T = v.tpb_tiles;
   const int first = blockIdx.x * T;
@@ -983,7 +996,7 @@ __global__ void __launch_bounds__(256, MINB) k_lattice(const View v, const S *__
 }
 
 template <class L, typename S, typename M>
-__global__ void __launch_bounds__(256, 4) k_boundary(const View v, const S *__restrict__ fin,
+__global__ void __launch_bounds__(256, 4) k_boundary(const __grid_constant__ View v, const S *__restrict__ fin,
                                                      S *__restrict__ fout) {
   __shared__ M stage[L::Q * stage_threads<L, M>()];  // populations, [direction][thread]
   boundary_tile<L, S, M>(v, fin, fout, v.btiles[blockIdx.x], stage);
@@ -1147,7 +1160,7 @@ __device__ __forceinline__ void tma_lattice(const View &v, const S *__restrict__
 }
 
 template <class L, typename S, typename M, int PHYS>
-__global__ void __launch_bounds__(256, 2) k_step_tma(const View v, const S *__restrict__ fin,
+__global__ void __launch_bounds__(256, 2) k_step_tma(const __grid_constant__ View v, const S *__restrict__ fin,
                                                      S *__restrict__ fout, int nstage, int stage_bytes) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem);

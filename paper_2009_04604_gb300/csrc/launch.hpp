@@ -27,7 +27,9 @@ cudaError_t prepare_step_tma(int lattice, int dtype, int phys, int bx, int by, l
 // two nodes per thread with at least 1..3 resident blocks per SM, 8: two nodes
 // per thread in 128-thread blocks, 9 and 10: the split step, whose lattice kernel
 // keeps at least 6 or 5 resident 256-thread blocks per SM and whose boundary
-// kernel runs with the launch lb (FP32/FP16/BF16). FP64 has a single variant.
+// kernel runs with the launch lb, 11 and 12: the combined kernel with at least 5
+// or 6 resident 256-thread blocks per SM (FP32/FP16/BF16). FP64 has a single
+// variant.
 cudaError_t launch_step(int lattice, int dtype, int variant, const View &v, const void *fin,
                         void *fout, const Launch &l, const Launch *lb = nullptr);
 cudaError_t launch_init(int lattice, int dtype, const View &v, void *fout, double rho, double ux,

@@ -739,7 +739,7 @@ int lbm_sim::download(HostGeometry &g) {
 // ---------------------------------------------------------------- launch configuration
 static bool valid_launch(const lbm_sim *h, int bx, int by, int variant, int tiles) {
   if (bx < 32 || bx % 32 || h->nxp % bx || by < 1 || bx * by > 256) return false;
-  if (variant < 0 || variant > 10 || tiles < 1 || tiles > 4) return false;
+  if (variant < 0 || variant > 12 || tiles < 1 || tiles > 4) return false;
   if (variant == 8 && bx * by != 128) return false;  // compiled for blocks of 128 threads
   if (h->dtype == LBM_F64 && variant != 0) return false;
   if (h->dtype == LBM_F64 && h->lattice == LBM_D3Q27 && bx * by > 128) return false;  // shared staging
@@ -780,7 +780,7 @@ extern "C" int lbm_autotune(lbm_handle h, int steps, int *bx, int *by, int *vari
   int best[4] = {save[0], save[1], save[2], save[3]};
   float best_ms = 1e30f;
   int rc = LBM_OK;
-  const int nvar = h->dtype == LBM_F64 ? 1 : 11;  // 4: TMA-staged persistent kernel; 5-8: node pairs; 9-10: split
+  const int nvar = h->dtype == LBM_F64 ? 1 : 13;  // 4: TMA; 5-8: node pairs; 9-10: split; 11-12: 5, 6 blocks
   const int tile_opts[3] = {1, 2, 4};
   for (int threads = 128; threads <= 256 && rc == LBM_OK; threads *= 2)
     for (int bxx = 32; bxx <= threads && rc == LBM_OK; bxx *= 2) {

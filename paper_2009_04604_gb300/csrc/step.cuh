@@ -119,6 +119,8 @@ cudaError_t launch_step_ls(int variant, const View &v, const void *fin, void *fo
   } else {
     if (variant == 9) return split_variant<L, S, M, 6>(v, fin, fout, l, lb);
     if (variant == 10) return split_variant<L, S, M, 5>(v, fin, fout, l, lb);
+    if (variant == 11) return step_variant<L, S, M, 5>(v, fin, fout, l);
+    if (variant == 12) return step_variant<L, S, M, 6>(v, fin, fout, l);
     if (variant == 4) {
       switch (phys_of(v)) {
         case PH_FORCE: return tma_launch<L, S, M, PH_FORCE>(v, fin, fout, l);

@@ -1,4 +1,5 @@
-"""The split step (launch variants 9 and 10) against the combined step kernel.
+"""The split step (launch variants 9 and 10), and the combined step kernel at 48
+and 40 registers (variants 11 and 12), against the combined kernel at 64.
 
 The split step runs the lattice tiles and the boundary-record tiles as two
 kernels side by side, each with its own register budget; every node runs the
@@ -82,9 +83,11 @@ CASES = ["duct", "random3d", "random2d_shear", "random27_trt", "porous", "shell"
 def test_split_step_is_bitwise_the_combined_step(case, dtype):
     ref = _make(case, dtype)
     ref.set_launch(32, 8, 3, 2)
-    runs = [_make(case, dtype) for _ in range(2)]
+    runs = [_make(case, dtype) for _ in range(4)]
     runs[0].set_launch(32, 8, 9, 1)
     runs[1].set_launch(32, 4, 10, 2)
+    runs[2].set_launch(32, 8, 11, 1)  # the combined kernel at 48 and 40 registers
+    runs[3].set_launch(64, 4, 12, 2)
     for n in (3, 40):  # direct launches, then a graph replay
         for s in [ref] + runs:
             s.step(n)
@@ -103,7 +106,7 @@ def test_split_step_limits():
     s.set_launch(64, 4, 9, 1)
     s.set_launch(32, 8, 10, 4)
     with pytest.raises(lbm.LBMError):
-        s.set_launch(32, 8, 11, 1)
+        s.set_launch(32, 8, 13, 1)
     s.set_options(lbm.BC_BFL, 1.0, (0, 0, 0), 0)  # one node per thread: BFL keeps the variant
     assert s.get_launch()[2] == 10
     s.step(4)

@@ -90,6 +90,9 @@ CASES = [
     (lbm.BC_ELIBB_FQ, lbm.F16, (64, 4, 9, 2)),
     (lbm.BC_ELIBB_F, lbm.BF16, (32, 8, 9, 1)),
     (lbm.BC_BFL, lbm.F32, (32, 8, 9, 1)),
+    (lbm.BC_ELIBB_F, lbm.F16, (32, 8, 12, 1)),
+    (lbm.BC_ELIBB_FQ, lbm.F32, (64, 4, 11, 2)),
+    (lbm.BC_BFL, lbm.F32, (32, 8, 12, 1)),
 ]
 
 

@@ -68,7 +68,7 @@ def test_random_geometry_f64_parity(bc, coll, lat, dims, xshift, force, tau):
     s.close()
 
 
-@pytest.mark.parametrize("variant", [0, 3, 4, 7, 9, 10])
+@pytest.mark.parametrize("variant", [0, 3, 4, 7, 9, 10, 12])
 @pytest.mark.parametrize("bc,coll", [(lbm.BC_ELIBB_UQ, lbm.COLL_BGK), (lbm.BC_ELIBB_FQ, lbm.COLL_TRT),
                                      (lbm.BC_ELIBB_U, lbm.COLL_TRT)])
 def test_sphere_duct_downscale_f32(bc, coll, variant):
