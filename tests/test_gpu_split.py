@@ -87,7 +87,7 @@ def test_split_step_is_bitwise_the_combined_step(case, dtype):
     runs[0].set_launch(32, 8, 9, 1)
     runs[1].set_launch(32, 4, 10, 2)
     runs[2].set_launch(32, 8, 11, 1)  # the combined kernel at 48 and 40 registers
-    runs[3].set_launch(64, 4, 12, 2)
+    runs[3].set_launch(32, 8, 12, 2)
     for n in (3, 40):  # direct launches, then a graph replay
         for s in [ref] + runs:
             s.step(n)
